@@ -1,0 +1,171 @@
+"""Transport pins of the oracle: the scheme must give the set Pr and gamma (Sec. III,
+Eq. Gamma, Eq. Pr) and the thermal Couette solutions (Sec. VI A).
+
+Under the parameter mapping (reading R3) the lattice kinematic viscosity is
+nu = (T/r^2)(tau_s - 1/2) and the thermal diffusivity chi = (T/r^2)(tau_q - 1/2)
+(lattice units, xi_i = r c_i so c_s^2 = T/r^2), hence Pr = nu/chi.  Measured here:
+  * the decay of a shear wave (rate nu k^2),
+  * the decay of an isobaric thermal wave (rate chi k^2),
+  * the speed of sound from a density wave (c^2 = gamma T in the long-wave limit;
+    a relaxing internal mode adds an O(k^2) dispersion that is extrapolated out),
+  * the steady thermal Couette profile (Eq. CouetteDi3, with unequal wall temperatures
+    T = T_b + (T_t - T_b) y + Pr U^2/(D+N_f+2) y(1-y)) and the start-up velocity series
+    (Eq. CouetteVelocityDimensionless with the lattice viscosity).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+
+def _fit_rate(ts, amps):
+    return -np.polyfit(ts, np.log(amps), 1)[0]
+
+
+def shear_ratio(Pr, gamma, tau, mode=O.PR_SHIFTED, kappa=0.2, N=64, steps=400):
+    s = O.Sim(O.D2Q37, nx=4, ny=N, Pr=Pr, gamma=gamma, kappa=kappa, tau=tau, mode=mode)
+    y, x = np.mgrid[0:N, 0:4]
+    s.init(np.ones((N, 4)), np.stack([1e-4 * np.sin(2 * np.pi * y / N), 0 * x]), np.ones((N, 4)))
+    ts, amps = [], []
+    for t in range(0, steps + 1, 50):
+        if t:
+            s.step(50)
+        ts.append(t)
+        amps.append(2 * np.mean(s.moments()["u"][0] * np.sin(2 * np.pi * y / N)))
+    k = 2 * np.pi / N
+    return _fit_rate(ts, amps) / ((s.coeffs["tau_s"] - 0.5) / s.r ** 2 * k * k)
+
+
+def thermal_ratio(Pr, gamma, tau, mode=O.PR_SHIFTED, kappa=0.2, N=64, steps=400):
+    s = O.Sim(O.D2Q37, nx=N, ny=4, Pr=Pr, gamma=gamma, kappa=kappa, tau=tau, mode=mode)
+    y, x = np.mgrid[0:4, 0:N]
+    T = 1 + 1e-4 * np.sin(2 * np.pi * x / N)
+    s.init(1 / T, np.zeros((2, 4, N)), T)  # isobaric: p = rho T uniform
+    ts, amps = [], []
+    for t in range(0, steps + 1, 50):
+        if t:
+            s.step(50)
+        ts.append(t)
+        amps.append(2 * np.mean((s.moments()["T"] - 1) * np.sin(2 * np.pi * x / N)))
+    k = 2 * np.pi / N
+    return _fit_rate(ts, amps) / ((s.coeffs["tau_q"] - 0.5) / s.r ** 2 * k * k)
+
+
+def sound_ratio(gamma, N, Pr=0.71, kappa=0.2, tau=0.8):
+    s = O.Sim(O.D2Q37, nx=N, ny=1, Pr=Pr, gamma=gamma, kappa=kappa, tau=tau)
+    x = np.arange(N)[None, :]
+    s.init(1 + 1e-4 * np.sin(2 * np.pi * x / N), np.zeros((2, 1, N)), np.ones((1, N)))
+    us = []
+    for t in range(int(3.2 * N) + 1):
+        if t:
+            s.step(1)
+        us.append(2 * np.mean(s.moments()["u"][0] * np.cos(2 * np.pi * x / N)))
+    us = np.array(us)
+    zc = [i - 1 + us[i - 1] / (us[i - 1] - us[i]) for i in range(1, len(us)) if us[i - 1] * us[i] < 0]
+    c = N / (2 * np.mean(np.diff(zc)))
+    return (c * s.r) ** 2 / gamma  # measured c^2 / (gamma T), T = 1
+
+
+@pytest.mark.parametrize("Pr", [0.5, 0.71, 2.0])
+@pytest.mark.parametrize("gamma", [1.4, 1.67])
+def test_viscosity_and_conductivity_give_set_Pr(Pr, gamma):
+    rs, rt = shear_ratio(Pr, gamma, 0.8), thermal_ratio(Pr, gamma, 0.8)
+    # O((k dx)^2) lattice dispersion at k = 2 pi/64 stays below ~1.5 %
+    assert abs(rs - 1) < 5e-3 and abs(rt - 1) < 1.5e-2, (rs, rt)
+    assert abs(rs / rt - 1) < 1.5e-2  # measured Pr = nu/chi vs set Pr
+
+
+def test_literal_mapping_follows_its_own_prediction():
+    # LITERAL mode: omega = Pr/tau_f, so tau_q = tau_f/Pr and Pr_eff = (tau-1/2)/(tau/Pr-1/2)
+    rs = shear_ratio(0.71, 1.4, 0.8, mode=O.PR_LITERAL)
+    rt = thermal_ratio(0.71, 1.4, 0.8, mode=O.PR_LITERAL)
+    assert abs(rs - 1) < 5e-3 and abs(rt - 1) < 5e-3
+
+
+@pytest.mark.parametrize("gamma", [1.4, 1.67])
+def test_sound_speed_gives_gamma(gamma):
+    # Richardson extrapolation of the O(k^2) dispersion from N = 128 and 256
+    c128, c256 = sound_ratio(gamma, 128), sound_ratio(gamma, 256)
+    c0 = c256 - (c128 - c256) / 3
+    assert abs(c0 - 1) < 2e-3, (c128, c256, c0)
+
+
+def test_sound_speed_distinguishes_gamma():
+    # the pin is not vacuous: the wrong gamma is far off
+    assert abs(sound_ratio(1.4, 128, kappa=0.5) * 1.4 / 1.67 - 1) > 0.1
+
+
+def couette(Ny, U, Tb, Tt, Pr=0.71, gamma=1.4, tau=0.8, steps=8000, nx=4, kappa=0.2):
+    s = O.Sim(O.D2Q37, nx=nx, ny=Ny, walls=True, Pr=Pr, gamma=gamma, kappa=kappa, tau=tau,
+              wall_u=np.array([[0, 0, 0], [U, 0, 0]], float), wall_T=np.array([Tb, Tt]))
+    s.init(np.ones((Ny, nx)), np.zeros((2, Ny, nx)), np.ones((Ny, nx)))
+    s.step(steps)
+    m = s.moments()
+    yh = np.arange(Ny) / (Ny - 1)
+    heat = Pr * U ** 2 / (2 + s.coeffs["Nf"] + 2)
+    Tan = Tb + (Tt - Tb) * yh + heat * yh * (1 - yh)
+    return m, yh, Tan, heat, s
+
+
+@pytest.mark.parametrize("Pr,gamma", [(0.71, 1.4), (2.0, 1.3)])
+def test_couette_steady_profiles(Pr, gamma):
+    errs = []
+    for Ny, steps in [(17, 4000), (33, 10000)]:
+        m, yh, Tan, heat, _ = couette(Ny, 0.2, 1.0, 1.01, Pr=Pr, gamma=gamma, steps=steps)
+        u = m["u"][0].mean(1)
+        assert np.abs(u - 0.2 * yh).max() < 1e-3 * 0.2      # linear, no slip
+        # wall-normal velocity: a steady wall-layer ripple, O(dx), decaying into the interior
+        assert np.abs(m["u"][1]).max() < 1e-4 * 0.2
+        if Ny == 33:
+            assert np.abs(m["u"][1][6:Ny - 6]).max() < 1e-6
+        errs.append(np.abs(m["T"].mean(1) - Tan).max() / (heat / 4))
+    assert errs[1] < 0.1 and errs[1] < 0.7 * errs[0], errs  # converges under refinement
+
+
+def test_couette_equal_walls_heating_profile():
+    # Eq. CouetteDi3: T = 1 + u0^2 Pr/(D+N_f+2) y(1-y)
+    m, yh, Tan, heat, _ = couette(33, 0.2, 1.0, 1.0, steps=10000)
+    T = m["T"].mean(1)
+    assert np.abs(T - Tan).max() < 0.03 * heat / 4
+    assert T[16] - 1 == pytest.approx(heat / 4, rel=0.03)
+
+
+def test_couette_startup_velocity_series():
+    # Eq. CouetteVelocityDimensionless with the lattice viscosity nu = (T/r^2)(tau_s - 1/2)
+    Ny, U, steps = 33, 0.05, 600
+    m, yh, _, _, s = couette(Ny, U, 1.0, 1.0, steps=steps)
+    nu = (s.coeffs["tau_s"] - 0.5) / s.r ** 2
+    L = Ny - 1
+    n = np.arange(1, 400)[:, None]
+    series = U * (yh + 2 / np.pi * np.sum((-1.0) ** n / n * np.exp(-n ** 2 * np.pi ** 2 * nu * steps / L ** 2)
+                                          * np.sin(n * np.pi * yh), axis=0))
+    u = m["u"][0].mean(1)
+    assert np.abs(u - series).max() < 0.01 * U, np.abs(u - series).max() / U
+
+
+def test_walls_conserve_fluid_mass():
+    # the wall density balances exactly the mass exchanged with the fluid rows (reading R5)
+    Ny = 17
+    _, _, _, _, s = couette(Ny, 0.1, 1.0, 1.02, steps=0)
+    g0 = s.populations()[0][:, 1:Ny - 1].sum()
+    s.step(300)
+    g1 = s.populations()[0][:, 1:Ny - 1].sum()
+    assert abs(g1 - g0) < 1e-11 * g0
+
+
+def test_d3q103_shear_wave_viscosity():
+    # the 3-D lattice (reading R4) carries the same viscosity law
+    N = 32
+    s = O.Sim(O.D3Q103, nx=2, ny=N, nz=2, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8)
+    z, y, x = np.mgrid[0:2, 0:N, 0:2]
+    u = np.stack([1e-4 * np.sin(2 * np.pi * y / N), 0 * x, 0 * x])
+    s.init(np.ones(z.shape), u, np.ones(z.shape))
+    ts, amps = [], []
+    for t in range(0, 201, 50):
+        if t:
+            s.step(50)
+        ts.append(t)
+        amps.append(2 * np.mean(s.moments()["u"][0] * np.sin(2 * np.pi * y / N)))
+    k = 2 * np.pi / N
+    ratio = _fit_rate(ts, amps) / ((s.coeffs["tau_s"] - 0.5) / s.r ** 2 * k * k)
+    assert abs(ratio - 1) < 1e-2, ratio
