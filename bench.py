@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of the fused ES-BGK stream-collide step on GB300 (one JSON line).
+
+Workload: 4096 x 4096 periodic thermal Taylor-Green field (U0 = 0.02, T amplitude 0.01),
+D2Q37, Pr = 0.71, gamma = 1.4 (N_f = 3), kappa = 0.2, tau = 0.528655 (nu = 0.02 lattice
+units).  One bench step = one lattice time step over the whole grid (one kernel launch).
+The headline `value` is FP32-storage MLUPS with the populations resident in HBM; the
+FP16 / BF16 shifted-storage forms are timed the same way, and the field error of every
+storage against the FP64 oracle is measured on a 128^2 copy of the field after 200 steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank runs its own replica (the step is one domain
+per GPU; scaling "weak"); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM peak, FP32 vs FP16-store at ≤1e-3 err; warm-start step savings"
+N_GRID = 4096
+PARAMS = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
+Q = 37
+KERNEL_SOURCES = ["kernels.cuh", "physics.cuh", "lattice.cuh", "dispatch.cuh"]
+
+
+def workload(storage):
+    return (f"thermal Taylor-Green {N_GRID}x{N_GRID} periodic, D2Q37, {storage} storage, Pr=0.71, gamma=1.4 "
+            f"(N_f=3), kappa=0.2, tau=0.528655 (nu=0.02 lu), U0=0.02, T amplitude 0.01")
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1611_02409_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_tag):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel source; else None."""
+    sha = kernel_src_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    pat = re.compile(r"traffic:\s*kernel=(\S+)\s+src_sha=(\S+)\s+bytes_per_launch=(\d+)")
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for m in pat.finditer(open(os.path.join(pdir, fn)).read()):
+            if m.group(1) == kernel_tag and m.group(2) == sha:
+                return int(m.group(3))
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_steps(torch, lbm, sim, steps, warmup, ws, clocks=None):
+    """Times `steps` single-step launches on the handle's stream: total and per launch."""
+    st = sim.stream
+    for _ in range(warmup):
+        lbm.lbm_step(sim.h, 1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for k in range(steps):
+        ev[k][0].record(st)
+        lbm.lbm_step(sim.h, 1)
+        ev[k][1].record(st)
+    t1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    total_ms = t0.elapsed_time(t1)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    return total_ms, float(np.mean(per_launch)), clk
+
+
+def accuracy_vs_oracle(lbm, n=128, steps=200):
+    """Field errors of every storage form against the FP64 oracle on an n^2 copy."""
+    from oracle import oracle as O
+    from paper_1611_02409_gb300 import inputs
+    fields = inputs.taylor_green_2d(n)
+    o = O.Sim(O.D2Q37, nx=n, ny=n, **PARAMS)
+    o.init(*fields)
+    o.step(steps)
+    mo = o.moments()
+    o.close()
+    out = {}
+    for storage in ("fp32", "fp16", "bf16"):
+        sim = lbm.Simulation(nx=n, ny=n, storage=storage, **PARAMS)
+        sim.init(*fields)
+        sim.step(steps)
+        mg = sim.moments()
+        sim.close()
+        errs = {}
+        for k in ("rho", "u", "T"):
+            d = np.linalg.norm((mg[k] - mo[k]).ravel())
+            errs[k] = float(d / np.linalg.norm(mo[k].ravel()))
+            errs[k + "_dev"] = float(d / np.linalg.norm((mo[k] - mo[k].mean()).ravel()))
+        errs["max_rel"] = max(errs["rho"], errs["u"], errs["T"])
+        out[storage] = errs
+    out["case"] = f"thermal Taylor-Green {n}x{n}, {steps} steps, same parameters"
+    return out
+
+
+def oracle_mlups(seconds=12.0, n=512):
+    """The oracle as it stands, on this host's cores, on an n^2 sample of the workload."""
+    from oracle import oracle as O
+    from paper_1611_02409_gb300 import inputs
+    o = O.Sim(O.D2Q37, nx=n, ny=n, **PARAMS)
+    o.init(*inputs.taylor_green_2d(n))
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n}x{n} thermal Taylor-Green sample of the workload, {steps} FP64 steps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1611_02409_gb300 import inputs
+    n = 512
+    o = O.Sim(O.D2Q37, nx=n, ny=n, **PARAMS)
+    o.init(*inputs.taylor_green_2d(n))
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    o.close()
+    v = n * n * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload("fp64 (oracle)"), "sample": f"{n}x{n} per step"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{n}x{n} thermal Taylor-Green sample per step, {args.steps} steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1611_02409_gb300 import build, inputs, lbm
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    lbm.lib()
+    n = N_GRID
+    cells = n * n
+    rho, u, T = inputs.taylor_green_2d(n)
+    peak, peak_kind = measured_peak()
+    results = {}
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    for storage, steps in (("fp32", args.steps), ("fp16", args.steps), ("bf16", max(args.steps // 2, 1))):
+        sim = lbm.Simulation(nx=n, ny=n, storage=storage, **PARAMS)
+        sim.init(rho, u, T)
+        clocks = Clocks(gpu_index) if storage == "fp32" else None
+        total_ms, launch_ms, clk = time_steps(torch, lbm, sim, steps, args.warmup, ws, clocks)
+        elem = 4 if storage == "fp32" else 2
+        b_cell = 2 * Q * 2 * elem
+        achieved = b_cell * cells / (launch_ms * 1e-3) / 1e9
+        results[storage] = dict(total_ms=total_ms, launch_ms=launch_ms, steps=steps, clocks=clk,
+                                mlups=ws * cells * steps / (total_ms * 1e-3) / 1e6, b_cell=b_cell,
+                                achieved=achieved)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    # end to end through the C ABI with host buffers: H2D of the fields, K steps, D2H of rho, u, T
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rho, h_u, h_T = pin(rho), pin(u), pin(T)
+    o_rho, o_u, o_T = (torch.empty(s, dtype=torch.float64).pin_memory() for s in ((n, n), (2, n, n), (n, n)))
+    sim = lbm.Simulation(nx=n, ny=n, storage="fp32", **PARAMS)
+    ptr = lambda t: t.numpy()
+    lbm.lbm_init_fields(sim.h, ptr(h_rho), ptr(h_u), ptr(h_T))
+    lbm.lbm_step(sim.h, args.warmup)
+    lbm.lbm_moments(sim.h, ptr(o_rho), ptr(o_u), ptr(o_T))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_init_fields(sim.h, ptr(h_rho), ptr(h_u), ptr(h_T))
+    lbm.lbm_step(sim.h, args.steps)
+    lbm.lbm_moments(sim.h, ptr(o_rho), ptr(o_u), ptr(o_T))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    sim.close()
+    h2d = 8 * cells * 4
+    d2h = 8 * cells * 4
+    extra = {}
+    if rank == 0:
+        extra["accuracy"] = accuracy_vs_oracle(lbm)
+        if ws == 1:
+            extra["cpu_baseline"] = oracle_mlups()
+    if rank != 0:
+        return
+    r32 = results["fp32"]
+    traffic = profiled_traffic("k_stream_collide<D2Q37,fp32,periodic>")
+    line = {
+        "metric": METRIC, "value": r32["mlups"], "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload("fp32"), "lattice": "D2Q37", "grid": [n, n], "storage": "fp32",
+                   "parallelism": f"{ws} independent replica(s), one domain per GPU",
+                   "l2": "inputs larger than L2: two 4.97 GB FP32 population buffers, no flush needed"},
+        "roofline": {"bound": "hbm", "achieved": r32["achieved"], "peak": peak, "unit": "GB/s",
+                     "frac": r32["achieved"] / peak, "traffic": traffic,
+                     "kernel": "k_stream_collide<D2Q37,fp32,periodic>",
+                     "algorithmic_bytes_per_cell": r32["b_cell"], "launch_ms": r32["launch_ms"],
+                     "peak_kind": f"{peak_kind} hbm_gbs"},
+        "clocks": r32["clocks"],
+        "gpu_launches": args.steps,
+        "e2e": {"value": ws * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "lbm_init_fields from pinned host rho,u,T + K steps + lbm_moments of rho,u,T to pinned "
+                        "host; bytes per step are the field copies divided by K"},
+        "storage_variants": {
+            s: {"mlups": results[s]["mlups"], "ms_per_step": results[s]["total_ms"] / results[s]["steps"],
+                "launch_ms": results[s]["launch_ms"], "achieved_gbs": results[s]["achieved"],
+                "frac": results[s]["achieved"] / peak, "algorithmic_bytes_per_cell": results[s]["b_cell"],
+                "steps": results[s]["steps"]} for s in ("fp16", "bf16")},
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

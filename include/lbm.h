@@ -1,0 +1,150 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) polyatomic ES-BGK lattice Boltzmann library.
+ *
+ * The scheme is that of Hu, Zhang, Du, Jin, Kong, "A lattice Boltzmann scheme with
+ * arbitrary Prandtl number and specific heat ratio based on the polyatomic ES-BGK model"
+ * (arXiv 1611.02409).  Each step pull-streams the mass populations g_i and the energy
+ * populations h_i, takes their moments, builds the ES-BGK Gaussian from the general
+ * Hermite-coefficient formula truncated at fourth order, relaxes both sets toward it and
+ * applies the walls (Sec. V, Eqs. DiscreteReductionG and DiscreteReductionH).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LBM_OK (0) or an LBM_ERR_* code; LBM_WARN_PR_RANGE (> 0 but not an
+ *     error) from lbm_create.  The text of the last error is lbm_last_error(handle).
+ *   - Units are the paper's dimensionless ones (Sec. V, "dimensionless variables"):
+ *     theta_0 = R_g T_0 = 1, so the sound speed of the isothermal gas is sqrt(T); the
+ *     lattice maps xi_i = r c_i with integer c_i, so one lattice spacing per time step is
+ *     r (lbm_lattice_info).  Lattice kinematic viscosity: (T/r^2)(tau - 1/2).
+ *   - Fields are SoA, [component][z][y][x] row-major, x fastest, over the Nx x Ny (x Nz)
+ *     domain, in double precision.  Pointers are device pointers unless the call's
+ *     `mem` argument is LBM_MEM_HOST; the caller owns them.
+ *   - The library owns the population buffers (allocated in lbm_create, freed in
+ *     lbm_destroy).  All device work is queued on the stream given to lbm_create;
+ *     lbm_step returns before the GPU finishes.  Device-side failures surface at the
+ *     next synchronising call (lbm_moments, lbm_diagnostics).
+ *   - A handle is not thread-safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_ERR_ARG 1        /* invalid argument or inadmissible parameters        */
+#define LBM_ERR_CUDA 2       /* a CUDA call failed (text in lbm_last_error)         */
+#define LBM_ERR_UNSTABLE 3   /* non-finite or non-positive density / temperature    */
+#define LBM_ERR_NOMEM 4      /* device allocation failed                            */
+#define LBM_WARN_PR_RANGE 100 /* Gaussian parameter nu < -1/2: outside the paper's
+                                2/3 <= Pr bound for its literal mapping (Sec. III)  */
+
+/* lattices: Sec. VI Table D2Q37; D3Q103 is this library's 3-D degree-9 lattice
+ * (shells 000,100,111,200,210,220,222,300,311,333 at the D2Q37 scale r) */
+#define LBM_D2Q37 1
+#define LBM_D3Q103 2
+
+/* parameter mapping (Sec. III Eq. Pr, Sec. V Eq. DiscreteReductionG):
+ *   LBM_PR_SHIFTED: tau_s = tau, tau_q = (tau - 1/2)/Pr + 1/2, omega = 1/tau_q and the
+ *                   Gaussian's nu from 1 - nu + kappa nu = tau_q/tau_s, so the lattice
+ *                   viscosity / conductivity ratio is the set Pr;
+ *   LBM_PR_LITERAL: omega = Pr/tau and 1 - nu + kappa nu = 1/Pr as printed. */
+#define LBM_PR_SHIFTED 0
+#define LBM_PR_LITERAL 1
+
+/* population storage (arithmetic is FP32 in every case): every precision holds
+ * (g_i - w_i)/w_i and (h_i - w_i N_f/2)/w_i, the deviations from the rest state
+ * rho = T = 1, u = 0 scaled by the weight; FP16 / BF16 round to nearest even. */
+#define LBM_FP32 0
+#define LBM_FP16 1
+#define LBM_BF16 2
+
+/* y boundaries */
+#define LBM_PERIODIC 0
+#define LBM_WALLS 1 /* hybrid kinetic (KBC) + non-equilibrium extrapolation walls (Sec. VI A) */
+
+/* memory space of field pointers */
+#define LBM_MEM_DEVICE 0
+#define LBM_MEM_HOST 1
+
+typedef struct lbm_params {
+    int lattice;          /* LBM_D2Q37 (D = 2) or LBM_D3Q103 (D = 3)                       */
+    double Pr;            /* target Prandtl number, > 0 (Eq. Pr)                          */
+    double gamma;         /* if > 0: N_f = 2/(gamma - 1) - D (Eq. Gamma); else N_f is used */
+    double N_f;           /* additional degrees of freedom, >= 0, real                     */
+    double kappa;         /* ES-BGK kappa in (0, 1]; kappa = 1 forces Pr = 1               */
+    double tau;           /* tau_f = tau / dt in lattice steps, > 1/2                      */
+    int pr_mode;          /* LBM_PR_SHIFTED or LBM_PR_LITERAL                              */
+    int storage;          /* LBM_FP32, LBM_FP16 or LBM_BF16                                */
+    int nx, ny, nz;       /* grid; nz = 1 for D = 2; nx, ny >= 1 (walls: ny >= 5)          */
+    int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D = 2 only); x (and z) periodic    */
+    double wall_u[2][3];  /* bottom (y = 0) / top (y = ny-1) wall velocity (tangential x)   */
+    double wall_T[2];     /* bottom / top wall temperature, > 0                            */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Validates *p, maps the parameters, derives the lattice in FP64, allocates the two
+ * population buffers on the current device and binds `stream` (a cudaStream_t, may be
+ * NULL for the legacy default stream).  On success *out receives the handle and the
+ * populations are those of rho = 1, u = 0, T = 1.  Returns LBM_OK, LBM_WARN_PR_RANGE
+ * (handle valid), LBM_ERR_ARG, LBM_ERR_NOMEM or LBM_ERR_CUDA (no handle). */
+int lbm_create(const lbm_params *p, void *stream, lbm_handle **out);
+
+/* Frees the handle and its device buffers (synchronises its stream first). */
+int lbm_destroy(lbm_handle *h);
+
+/* Text of the last error on this handle ("" if none); a static string for h == NULL
+ * describing the last lbm_create failure. */
+const char *lbm_last_error(const lbm_handle *h);
+
+/* Lattice of a handle: D, Q, scale r, integer velocities c[Q][3] and weights w[Q]
+ * (host arrays of at least Q entries, each may be NULL), in the library's own order. */
+int lbm_lattice_info(const lbm_handle *h, int *D, int *Q, double *r, int *c, double *w);
+
+/* Mapped coefficients: out[0..5] = N_f, omega, nu (Gaussian), tau_s, tau_q, kappa. */
+int lbm_coefficients(const lbm_handle *h, double *out);
+
+/* Handle-free host helpers (no device work): the lattice as lbm_create derives it
+ * (weights re-solved in FP64 from the degree-9 moment conditions, Sec. VI A), and the
+ * mapping of a parameter set to out[0..5] as in lbm_coefficients.  lbm_map_params
+ * returns LBM_ERR_ARG for an inadmissible set and LBM_WARN_PR_RANGE as lbm_create does. */
+int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w);
+int lbm_map_params(const lbm_params *p, double *out);
+
+/* Sets every population (domain and wall ghost rows) to the discrete equilibrium of the
+ * fields with Lambda = T delta: g_i = G_i(rho, u, T delta), h_i = (N_f/2) T G_i.  rho[n],
+ * u[D][n], T[n] with n = Nx Ny Nz; ghost rows take the nearest domain row's field.
+ * `mem` = LBM_MEM_DEVICE or LBM_MEM_HOST (host arrays are staged through a device copy
+ * on the handle's stream).  Resets the step counter. */
+int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const double *T, int mem);
+
+/* Queues nsteps fused pull-stream + collide steps (+ the wall kernel when bc_y is
+ * LBM_WALLS) on the handle's stream.  nsteps >= 0. */
+int lbm_step(lbm_handle *h, int nsteps);
+
+/* Macroscopic fields of the stored (post-collision) populations, per domain cell:
+ * rho[n]; u[D][n]; T[n] = T_eq; Pi[D(D+1)/2][n] = rho sigma (xx, xy, (xz), yy, (yz), (zz));
+ * q[D][n] = sum_i g_i |xi_i - u|^2 (xi_i - u)/2 + h_i (xi_i - u).  Any pointer may be
+ * NULL.  Synchronises the handle's stream. */
+int lbm_moments(lbm_handle *h, double *rho, double *u, double *T, double *Pi, double *q, int mem);
+
+/* FP64 global diagnostics over the domain (deterministic reduction):
+ * out[0] mass sum rho; out[1..3] momentum sum rho u; out[4] total energy
+ * sum rho E = sum_i (xi_i^2 g_i / 2 + h_i); out[5] residual
+ * max_{X in {u_x, T}} ||X - X_prev||_2 / (m ||X||_2) against the fields of the previous
+ * lbm_diagnostics call m steps earlier (0 on the first call); out[6] number of cells with
+ * a non-finite value, rho <= 0 or T <= 0; out[7] steps taken since lbm_init_fields.
+ * Synchronises; returns LBM_ERR_UNSTABLE when out[6] > 0. */
+int lbm_diagnostics(lbm_handle *h, double *out);
+
+/* Checkpoint / resume: copies the domain populations (not ghost rows) as FP64 absolute
+ * values g[Q][n], h[Q][n] (host or device per `mem`) out of / into the handle. */
+int lbm_get_populations(lbm_handle *h, double *g, double *hh, int mem);
+int lbm_set_populations(lbm_handle *h, const double *g, const double *hh, int mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

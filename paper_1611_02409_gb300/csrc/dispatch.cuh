@@ -1,0 +1,106 @@
+// Host-side launch wrappers of the kernels for one lattice (included by one .cu per
+// lattice, which instantiates them and exports an Ops table to the C-ABI layer).
+#pragma once
+#include "kernels.cuh"
+#include "ops.h"
+
+namespace lbm {
+
+template <int LAT> KParams<LAT> make_kparams(const Ctx &c)
+{
+    KParams<LAT> kp;
+    kp.nx = c.nx;
+    kp.ny = c.ny;
+    kp.nz = c.nz;
+    kp.nys = c.nys;
+    kp.gh = c.gh;
+    kp.y0 = c.walls ? 1 : 0;
+    kp.ny_comp = c.walls ? c.ny - 2 : c.ny;
+    kp.plane = c.plane;
+    kp.omega = (float)c.omega;
+    kp.kappa = (float)c.kappa;
+    kp.a_tr = (float)c.a_tr;
+    kp.a_sig = (float)c.a_sig;
+    kp.Nf = (float)c.Nf;
+    kp.halfNf = (float)(0.5 * c.Nf);
+    kp.r = (float)c.r;
+    for (int i = 0; i < KParams<LAT>::Q; ++i) kp.w[i] = (float)c.w[i];
+    return kp;
+}
+
+template <int LAT, int ST> struct Launch {
+    using T = typename Storage<ST>::T;
+    static constexpr int kTx = 128;
+
+    static dim3 rows_grid(const Ctx &c, int rows) { return dim3((c.nx + kTx - 1) / kTx, rows, c.nz); }
+
+    static void init(const Ctx &c, void *dst, const double *rho, const double *u, const double *T_, cudaStream_t st)
+    {
+        k_init<LAT, ST><<<rows_grid(c, c.nys), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_);
+    }
+    static void step(const Ctx &c, const void *src, void *dst, cudaStream_t st)
+    {
+        const KParams<LAT> kp = make_kparams<LAT>(c);
+        const dim3 grid = rows_grid(c, kp.ny_comp);
+        const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
+        if (c.walls)
+            k_stream_collide<LAT, ST, true><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
+        else
+            k_stream_collide<LAT, ST, false><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
+    }
+    static void walls(const Ctx &c, void *buf, cudaStream_t st)
+    {
+        if constexpr (Lattice<LAT>::D == 2) {
+            WallParams wp;
+            for (int b = 0; b < 2; ++b) {
+                for (int d = 0; d < 3; ++d) wp.uw[b][d] = (float)c.wall_u[b][d];
+                wp.thw[b] = (float)(c.wall_T[b] - 1.0);
+            }
+            k_walls<LAT, ST><<<dim3((c.nx + 63) / 64, 2, 1), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), wp);
+        }
+    }
+    static void moments(const Ctx &c, const void *buf, double *rho, double *u, double *T_, double *Pi, double *q,
+                        cudaStream_t st)
+    {
+        k_moments<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), rho, u, T_,
+                                                             Pi, q);
+    }
+    static void diag(const Ctx &c, const void *buf, float *snap, int have_snap, double *partials, int nblk,
+                     cudaStream_t st)
+    {
+        k_diag<LAT, ST><<<nblk, kDiagThreads, 0, st>>>((const T *)buf, make_kparams<LAT>(c), snap, have_snap,
+                                                       partials);
+    }
+    static void get_pops(const Ctx &c, const void *buf, double *g, double *h, cudaStream_t st)
+    {
+        k_get_pops<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), g, h);
+    }
+    static void set_pops(const Ctx &c, void *buf, const double *g, const double *h, cudaStream_t st)
+    {
+        k_set_pops<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), g, h);
+    }
+};
+
+template <int LAT, int ST> Ops make_ops_st()
+{
+    Ops o;
+    o.init = &Launch<LAT, ST>::init;
+    o.step = &Launch<LAT, ST>::step;
+    o.walls = &Launch<LAT, ST>::walls;
+    o.moments = &Launch<LAT, ST>::moments;
+    o.diag = &Launch<LAT, ST>::diag;
+    o.get_pops = &Launch<LAT, ST>::get_pops;
+    o.set_pops = &Launch<LAT, ST>::set_pops;
+    return o;
+}
+
+template <int LAT> Ops make_ops(int storage)
+{
+    switch (storage) {
+    case ST_FP16: return make_ops_st<LAT, ST_FP16>();
+    case ST_BF16: return make_ops_st<LAT, ST_BF16>();
+    default: return make_ops_st<LAT, ST_FP32>();
+    }
+}
+
+} // namespace lbm

@@ -1,0 +1,424 @@
+// Kernels of the ES-BGK lattice Boltzmann step, templated on lattice and storage.
+//
+// Layout in HBM: two population buffers (ping-pong), each holding 2Q planes
+// [set][i][z][y][x] (set 0 = g, set 1 = h), x fastest.  In wall mode each plane has
+// ny + 2 gh rows: gh = 2 ghost rows beyond each wall row (rows y = 0 and y = ny-1).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "physics.cuh"
+
+namespace lbm {
+
+constexpr int kDiagNV = 10;      // diagnostics partial sums per block
+constexpr int kDiagThreads = 256;
+
+// x - C wrapped into [0, n); `small` grids (n < 4) take the general modulo path.
+template <int C> __device__ __forceinline__ int wrap_sub(int x, int n, bool small)
+{
+    int v = x - C;
+    if (small) return ((v % n) + n) % n;
+    if constexpr (C > 0) {
+        if (v < 0) v += n;
+    } else if constexpr (C < 0) {
+        if (v >= n) v -= n;
+    }
+    return v;
+}
+
+template <int LAT>
+__device__ __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, int ys, int z)
+{
+    return ((long long)z * kp.nys + ys) * kp.nx + x;
+}
+
+// Relax one opposite pair (I, I+1) and store it: s' = s + omega(G~/w - s), same for t.
+template <int LAT, int ST>
+__device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ dst, long long o,
+                                            long long plane, int I, float om, const EqScal &z,
+                                            float q, float s, float t)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    const float Gs = fmaf(z.rho, q, z.drho);
+    const float Ht = fmaf(z.hr, q, z.hb);
+    Storage<ST>::st(dst + (long long)I * plane + o, fmaf(om, Gs - s, s));
+    Storage<ST>::st(dst + (long long)(Q + I) * plane + o, fmaf(om, Ht - t, t));
+}
+
+// Collide the gathered populations s[], t[] of one cell and store them at offset o.
+template <int LAT, int ST>
+__device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const float *s, const float *t,
+                                              typename Storage<ST>::T *__restrict__ dst, long long o)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    RawMoments<D> m;
+    raw_moments<LAT>(kp, s, t, m);
+    CellState<D> c;
+    cell_state<LAT>(kp, m, c);
+    EqState<D> e;
+    es_state<LAT>(kp, c, e);
+    PolyCoef<D> pc;
+    poly_coeffs<D>(e, kp.r, pc);
+    const EqScal z = eq_scalars<D>(e, kp.halfNf);
+    relax_store<LAT, ST>(dst, o, kp.plane, 0, kp.omega, z, pc.k[0], s[0], t[0]);
+    static_for<0, (Q - 1) / 2>([&](auto PP) {
+        constexpr int I = 1 + 2 * decltype(PP)::value;
+        float E, O;
+        poly_eval_pair<LAT, I>(pc, E, O);
+        relax_store<LAT, ST>(dst, o, kp.plane, I, kp.omega, z, E + O, s[I], t[I]);
+        relax_store<LAT, ST>(dst, o, kp.plane, I + 1, kp.omega, z, E - O, s[I + 1], t[I + 1]);
+    });
+}
+
+// Fused pull-stream + collide (Eqs. DiscreteReductionG / DiscreteReductionH): one thread
+// per cell of row y = y0 + blockIdx.y (plane z = blockIdx.z), all 2Q populations in
+// registers.  Periodic in x (and z, y when !WALLS); with WALLS the rows y - c_y reach
+// into the ghost rows, which the wall kernel filled after the previous step.
+template <int LAT, int ST, bool WALLS>
+__global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<ST>::T *__restrict__ src,
+                                                        typename Storage<ST>::T *__restrict__ dst,
+                                                        const KParams<LAT> kp, int small_x, int small_y,
+                                                        int small_z)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    using S = Storage<ST>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y + kp.y0;
+    const int z = blockIdx.z;
+    float s[Q], t[Q];
+    static_for<0, Q>([&](auto II) {
+        constexpr int I = decltype(II)::value;
+        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
+        const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+        int ys;
+        if constexpr (WALLS) ys = y - cy + kp.gh;
+        else ys = wrap_sub<cy>(y, kp.ny, small_y);
+        int zs = z;
+        if constexpr (D == 3) zs = wrap_sub<cz>(z, kp.nz, small_z);
+        const long long idx = cell_index<LAT>(kp, xs, ys, zs);
+        s[I] = S::ld(src + (long long)I * kp.plane + idx);
+        t[I] = S::ld(src + (long long)(Q + I) * kp.plane + idx);
+    });
+    (void)small_z;
+    const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
+    collide_store<LAT, ST>(kp, s, t, dst, o);
+}
+
+// Scaled equilibrium populations of (rho, u, T) with Lambda = T delta into s[], t[].
+template <int LAT>
+__device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho, const float (&u)[Lattice<LAT>::D],
+                                             float th, float *s, float *t)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    EqState<D> e;
+    maxwell_state<D>(drho, u, th, e);
+    PolyCoef<D> pc;
+    poly_coeffs<D>(e, kp.r, pc);
+    const EqScal z = eq_scalars<D>(e, kp.halfNf);
+    s[0] = fmaf(z.rho, pc.k[0], z.drho);
+    t[0] = fmaf(z.hr, pc.k[0], z.hb);
+    static_for<0, (Q - 1) / 2>([&](auto PP) {
+        constexpr int I = 1 + 2 * decltype(PP)::value;
+        float E, O;
+        poly_eval_pair<LAT, I>(pc, E, O);
+        s[I] = fmaf(z.rho, E + O, z.drho);
+        t[I] = fmaf(z.hr, E + O, z.hb);
+        s[I + 1] = fmaf(z.rho, E - O, z.drho);
+        t[I + 1] = fmaf(z.hr, E - O, z.hb);
+    });
+}
+
+// Initial populations (equilibrium of the fields, Lambda = T delta) for every stored
+// cell; ghost rows take the nearest domain row's field.  Fields are FP64 device arrays.
+template <int LAT, int ST>
+__global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<LAT> kp,
+                       const double *__restrict__ rho, const double *__restrict__ u,
+                       const double *__restrict__ T)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int ys = blockIdx.y, z = blockIdx.z;
+    int y = ys - kp.gh;
+    y = y < 0 ? 0 : (y > kp.ny - 1 ? kp.ny - 1 : y);
+    const long long n = (long long)kp.nx * kp.ny * kp.nz;
+    const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
+    float uu[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) uu[a] = (float)u[a * n + f];
+    float s[Q], t[Q];
+    maxwell_pops<LAT>(kp, (float)(rho[f] - 1.0), uu, (float)(T[f] - 1.0), s, t);
+    const long long o = cell_index<LAT>(kp, x, ys, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        Storage<ST>::st(dst + (long long)i * kp.plane + o, s[i]);
+        Storage<ST>::st(dst + (long long)(Q + i) * kp.plane + o, t[i]);
+    }
+}
+
+template <int LAT, int ST>
+__device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> &kp,
+                                          long long o, float *s, float *t)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        s[i] = Storage<ST>::ld(buf + (long long)i * kp.plane + o);
+        t[i] = Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o);
+    }
+}
+
+// Wall procedure (hybrid KBC + NEEP, Sec. VI A), one thread per (column x, wall b),
+// run on the post-collision buffer after the fluid rows were updated.  Boundary row at
+// distance k (k = 0 wall row, 1..gh ghost rows): state u_k = u_w - k(u_1 - u_w),
+// T_k = T_w - k(T_1 - T_w) from the first fluid row's (u_1, T_1); populations
+// rho_w G(1, u_k, T_k delta) + the first fluid row's non-equilibrium (populations minus
+// their Maxwellian).  rho_w balances exactly the mass the fluid sends into these rows
+// in the next streaming against the mass the rows send back.
+struct WallParams {
+    float uw[2][3];
+    float thw[2];   // T_w - 1
+};
+
+template <int LAT, int ST>
+__global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const WallParams wp)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    static_assert(D == 2, "walls are 2-D");
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int b = blockIdx.y;
+    const int n = b == 0 ? 1 : -1;
+    const int yw = b == 0 ? 0 : kp.ny - 1;
+    const int small_x = kp.nx < 4;
+    float s1[Q], t1[Q];
+    load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, yw + n + kp.gh, 0), s1, t1);
+    RawMoments<D> m;
+    raw_moments<LAT>(kp, s1, t1, m);
+    CellState<D> c;
+    cell_state<LAT>(kp, m, c);
+    float ms[Q], mt[Q];
+    maxwell_pops<LAT>(kp, c.drho, c.u, c.th_eq, ms, mt);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {  // non-equilibrium of the first fluid row
+        s1[i] -= ms[i];
+        t1[i] -= mt[i];
+    }
+    float uk[3][D], thk[3];
+    for (int k = 0; k <= 2; ++k) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) uk[k][a] = wp.uw[b][a] - k * (c.u[a] - wp.uw[b][a]);
+        thk[k] = wp.thw[b] - k * (c.th_eq - wp.thw[b]);
+    }
+    // unit-density equilibria of the boundary rows (deviation / w): drho = 0
+    float gk[3][Q], hk[3][Q];
+    for (int k = 0; k <= 2; ++k) maxwell_pops<LAT>(kp, 0.f, uk[k], thk[k], gk[k], hk[k]);
+    // leaving - B - A, all in deviation form: the w parts of "leaving" and "A" cancel.
+    float Ld = 0.f, Bd = 0.f, Ad = 0.f, W = 0.f;
+    static_for<0, Q>([&](auto II) {
+        constexpr int I = decltype(II)::value;
+        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>();
+        if constexpr (cy != 0) {
+            const int cn = cy * n;
+            const float w = kp.w[I];
+            if (cn < 0) {
+                const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+                for (int sdist = 1; sdist <= -cn; ++sdist)
+                    Ld = fmaf(w, Storage<ST>::ld(buf + (long long)I * kp.plane
+                                                 + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, 0)), Ld);
+            } else {
+                W = fmaf((float)cn, w, W);
+                Bd = fmaf((float)cn * w, s1[I], Bd);
+                for (int k = 0; k < cn; ++k) Ad = fmaf(w, gk[k][I], Ad);
+            }
+        }
+    });
+    const float drw = (Ld - Bd - Ad) / (W + Ad);   // rho_w - 1
+    const float rw = 1.f + drw;
+    for (int k = 0; k <= 2; ++k) {
+        const long long o = cell_index<LAT>(kp, x, yw - n * k + kp.gh, 0);
+        // G(rho_w, u_k, T_k)/w - 1 = drw + rw * gk;   (N_f/2)(rho_w T_k G/w - 1) = drw' + rw * hk
+        const float hb = kp.halfNf * drw;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            Storage<ST>::st(buf + (long long)i * kp.plane + o, fmaf(rw, gk[k][i], drw) + s1[i]);
+            Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, fmaf(rw, hk[k][i], hb) + t1[i]);
+        }
+    }
+}
+
+// Macroscopic fields of the stored populations (FP64 out, any pointer may be null).
+template <int LAT, int ST>
+__global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp,
+                          double *rho, double *u, double *T, double *Pi, double *q)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    float s[Q], t[Q];
+    load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
+    RawMoments<D> m;
+    raw_moments<LAT>(kp, s, t, m);
+    CellState<D> c;
+    cell_state<LAT>(kp, m, c);
+    const long long n = (long long)kp.nx * kp.ny * kp.nz;
+    const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
+    if (rho) rho[f] = 1.0 + (double)c.drho;
+    if (u)
+        for (int a = 0; a < D; ++a) u[a * n + f] = c.u[a];
+    if (T) T[f] = 1.0 + (double)c.th_eq;
+    if (Pi) {
+        int k = 0;
+        for (int a = 0; a < D; ++a)
+            for (int bb = a; bb < D; ++bb)
+                Pi[(k++) * n + f] = (double)c.rho * ((a == bb ? 1.0 : 0.0) + (double)c.sdev[a][bb]);
+    }
+    if (q) {
+        // q_a = sum g |v|^2 v_a / 2 + sum h v_a, v = xi - u; the rest-state (w) part is
+        // -u_a (D + 2 + u^2 + N_f)/2 in closed form (degree-3 moments of the lattice).
+        float u2 = 0.f;
+        for (int a = 0; a < D; ++a) u2 += c.u[a] * c.u[a];
+        float qa[D];
+        for (int a = 0; a < D; ++a) qa[a] = -0.5f * c.u[a] * (D + 2 + u2 + kp.Nf);
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            const float w = kp.w[I];
+            float v[D], v2 = 0.f;
+            static_for<0, D>([&](auto AA) {
+                constexpr int a = decltype(AA)::value;
+                v[a] = kp.r * (float)cv<LAT, I, a>() - c.u[a];
+                v2 += v[a] * v[a];
+            });
+            const float gd = w * s[I], hd = w * t[I];
+            for (int a = 0; a < D; ++a) qa[a] += (0.5f * v2 * gd + hd) * v[a];
+        });
+        for (int a = 0; a < D; ++a) q[a * n + f] = qa[a];
+    }
+}
+
+template <typename Tv> __device__ __forceinline__ Tv warp_sum(Tv v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sums of kDiagNV doubles, written by thread 0 to out[0..kDiagNV).
+__device__ __forceinline__ void block_sums(double (&acc)[kDiagNV], double *out)
+{
+    __shared__ double sh[kDiagThreads / 32][kDiagNV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < kDiagNV; ++v) {
+        double x = warp_sum(acc[v]);
+        if (lane == 0) sh[wid][v] = x;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int v = 0; v < kDiagNV; ++v) {
+            double x = lane < kDiagThreads / 32 ? sh[lane][v] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) out[v] = x;
+        }
+    }
+}
+
+// FP64 diagnostics, stage 1: a fixed grid strides over the domain cells, each block
+// writes kDiagNV partial sums: {sum drho, sum rho u (3), sum (rho E - rho E_rest),
+// sum du_x^2, sum u_x^2, sum dT^2, sum T^2, bad cells}.  Snapshots u_x, T - 1 for the
+// next call's residual.
+template <int LAT, int ST>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const typename Storage<ST>::T *__restrict__ buf,
+                                                        const KParams<LAT> kp, float *snap, int have_snap,
+                                                        double *partials)
+{
+    constexpr int D = Lattice<LAT>::D;
+    constexpr int Q = Lattice<LAT>::Q;
+    double acc[kDiagNV];
+#pragma unroll
+    for (int v = 0; v < kDiagNV; ++v) acc[v] = 0.0;
+    const long long n = (long long)kp.nx * kp.ny * kp.nz;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < n;
+         f += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(f % kp.nx);
+        const long long yz = f / kp.nx;
+        const int y = (int)(yz % kp.ny), z = (int)(yz / kp.ny);
+        float s[Q], t[Q];
+        load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
+        RawMoments<D> m;
+        raw_moments<LAT>(kp, s, t, m);
+        CellState<D> c;
+        cell_state<LAT>(kp, m, c);
+        acc[0] += (double)m.drho;
+        for (int a = 0; a < D; ++a) acc[1 + a] += (double)kp.r * (double)m.J[a];
+        float trM = 0.f;
+        for (int a = 0; a < D; ++a) trM += m.M[a][a];
+        acc[4] += 0.5 * (double)kp.r * (double)kp.r * (double)trM + (double)m.H;
+        const float ux = c.u[0], th = c.th_eq;
+        bool ok = isfinite(c.rho) && isfinite(th) && c.rho > 0.f && 1.f + th > 0.f;
+        for (int a = 0; a < D; ++a) ok = ok && isfinite(c.u[a]);
+        acc[9] += ok ? 0.0 : 1.0;
+        acc[6] += (double)ux * ux;
+        acc[8] += (1.0 + th) * (1.0 + th);
+        if (have_snap) {
+            const double du = (double)ux - snap[f], dT = (double)th - snap[n + f];
+            acc[5] += du * du;
+            acc[7] += dT * dT;
+        }
+        snap[f] = ux;
+        snap[n + f] = th;
+    }
+    block_sums(acc, partials + (long long)blockIdx.x * kDiagNV);
+}
+
+// Stage 2: one block sums the partials in a fixed order (deterministic).
+__global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double *__restrict__ partials, int nblk,
+                                                              double *out);
+
+// Domain populations to / from absolute FP64 [i][z][y][x].
+template <int LAT, int ST>
+__global__ void k_get_pops(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, double *g,
+                           double *h)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long n = (long long)kp.nx * kp.ny * kp.nz;
+    const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
+    const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
+    for (int i = 0; i < Q; ++i) {
+        const double w = kp.w[i];
+        if (g) g[i * n + f] = w * (1.0 + (double)Storage<ST>::ld(buf + (long long)i * kp.plane + o));
+        if (h) h[i * n + f] = w * ((double)kp.halfNf + (double)Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o));
+    }
+}
+
+template <int LAT, int ST>
+__global__ void k_set_pops(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const double *g,
+                           const double *h)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long n = (long long)kp.nx * kp.ny * kp.nz;
+    const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
+    const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
+    for (int i = 0; i < Q; ++i) {
+        const double w = kp.w[i];
+        Storage<ST>::st(buf + (long long)i * kp.plane + o, (float)(g[i * n + f] / w - 1.0));
+        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, (float)(h[i * n + f] / w - (double)kp.halfNf));
+    }
+}
+
+} // namespace lbm

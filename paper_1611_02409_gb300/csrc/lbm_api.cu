@@ -1,0 +1,444 @@
+// C ABI of the library (declared in include/lbm.h): handle lifetime, parameter mapping,
+// buffers, and the host side of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "kernels.cuh"
+#include "ops.h"
+
+struct lbm_handle {
+    lbm_params p;
+    int D, Q;
+    double r;
+    int c[128][3];
+    double w[128];
+    double Nf, omega, nuG, tau_s, tau_q;
+    lbm::Ctx ctx;
+    lbm::Ops ops;
+    cudaStream_t stream;
+    size_t elem;           // bytes per stored population
+    size_t buf_elems;      // elements per population buffer (2 Q planes)
+    void *buf[2];
+    int cur;
+    long long steps;
+    // scratch
+    double *d_partials;
+    int diag_blocks;
+    double *d_out;
+    double *h_out;         // pinned
+    float *d_snap;         // u_x and T - 1 of the previous diagnostics call
+    int have_snap;
+    long long snap_step;
+    double *d_stage;       // device staging for host-memory field I/O
+    size_t stage_bytes;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int set_err(lbm_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(lbm_handle *h, cudaError_t e, const char *what)
+{
+    return set_err(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CK(h, call)                                                                                        \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);                                                 \
+    } while (0)
+
+long long ncell(const lbm_handle *h) { return (long long)h->p.nx * h->p.ny * h->p.nz; }
+
+int ensure_stage(lbm_handle *h, size_t bytes)
+{
+    if (h->stage_bytes >= bytes) return LBM_OK;
+    if (h->d_stage) cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->d_stage, bytes);
+    if (e != cudaSuccess) return set_err(h, LBM_ERR_NOMEM, std::string("staging allocation: ") + cudaGetErrorString(e));
+    h->stage_bytes = bytes;
+    return LBM_OK;
+}
+
+} // namespace
+
+namespace lbm {
+__global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double *__restrict__ partials, int nblk,
+                                                              double *out)
+{
+    double acc[kDiagNV];
+#pragma unroll
+    for (int v = 0; v < kDiagNV; ++v) acc[v] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < kDiagNV; ++v) acc[v] += partials[(long long)b * kDiagNV + v];
+    block_sums(acc, out);
+}
+
+void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st)
+{
+    k_diag_final<<<1, kDiagThreads, 0, st>>>(partials, nblk, out);
+}
+} // namespace lbm
+
+extern "C" {
+
+const char *lbm_last_error(const lbm_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+struct Mapped {
+    int D;
+    double Nf, omega, nuG, tau_s, tau_q;
+    bool warn;
+};
+
+// Validation and parameter mapping shared by lbm_create and lbm_map_params.
+static int map_params(const lbm_params &p, Mapped &m)
+{
+    if (p.lattice == LBM_D2Q37) m.D = 2;
+    else if (p.lattice == LBM_D3Q103) m.D = 3;
+    else return set_err(nullptr, LBM_ERR_ARG, "unknown lattice");
+    const int D = m.D;
+    if (p.nx < 1 || p.ny < 1 || (D == 3 && p.nz < 1)) return set_err(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
+    if ((long long)p.nx * p.ny * (D == 3 ? p.nz : 1) > (1LL << 31) - 1)
+        return set_err(nullptr, LBM_ERR_ARG, "grid too large");
+    if (p.bc_y != LBM_PERIODIC && p.bc_y != LBM_WALLS) return set_err(nullptr, LBM_ERR_ARG, "bad bc_y");
+    if (p.bc_y == LBM_WALLS && (D != 2 || p.ny < 5))
+        return set_err(nullptr, LBM_ERR_ARG, "walls need D = 2 and ny >= 5");
+    if (p.storage < LBM_FP32 || p.storage > LBM_BF16) return set_err(nullptr, LBM_ERR_ARG, "bad storage");
+    if (p.pr_mode != LBM_PR_SHIFTED && p.pr_mode != LBM_PR_LITERAL) return set_err(nullptr, LBM_ERR_ARG, "bad pr_mode");
+    if (!(p.Pr > 0) || !(p.tau > 0.5) || !(p.kappa > 0) || !(p.kappa <= 1))
+        return set_err(nullptr, LBM_ERR_ARG, "need Pr > 0, tau > 1/2, 0 < kappa <= 1");
+    // Eq. Gamma: N_f = 2/(gamma - 1) - D
+    double Nf = p.gamma > 0 ? 2.0 / (p.gamma - 1.0) - D : p.N_f;
+    if (p.gamma > 0 && !(p.gamma > 1.0)) return set_err(nullptr, LBM_ERR_ARG, "gamma must exceed 1");
+    if (Nf < -1e-12 || !std::isfinite(Nf)) return set_err(nullptr, LBM_ERR_ARG, "N_f < 0 (gamma above (D+2)/D)");
+    if (Nf < 0) Nf = 0;
+    if (p.kappa == 1.0 && std::fabs(p.Pr - 1.0) > 1e-12)
+        return set_err(nullptr, LBM_ERR_ARG, "kappa = 1 leaves no freedom for Pr != 1");
+    if (p.bc_y == LBM_WALLS && !(p.wall_T[0] > 0 && p.wall_T[1] > 0))
+        return set_err(nullptr, LBM_ERR_ARG, "wall temperatures must be > 0");
+    if (p.pr_mode == LBM_PR_LITERAL) {
+        m.omega = p.Pr / p.tau;             // rate Pr/tau_f (Eq. DiscreteReductionG)
+        m.tau_s = p.tau;
+        m.tau_q = p.tau / p.Pr;
+        m.nuG = p.kappa < 1 ? (1.0 - 1.0 / p.Pr) / (1.0 - p.kappa) : 0.0; // 1 - nu + kappa nu = 1/Pr
+    } else {
+        m.tau_s = p.tau;
+        m.tau_q = 0.5 + (p.tau - 0.5) / p.Pr; // viscosity / conductivity ratio = Pr
+        m.omega = 1.0 / m.tau_q;
+        m.nuG = p.kappa < 1 ? (1.0 - m.tau_q / m.tau_s) / (1.0 - p.kappa) : 0.0;
+    }
+    if (!(m.omega > 0 && m.omega < 2)) return set_err(nullptr, LBM_ERR_ARG, "relaxation rate outside (0, 2)");
+    m.Nf = Nf;
+    m.warn = m.nuG < -0.5;
+    return LBM_OK;
+}
+
+int lbm_map_params(const lbm_params *p, double *out)
+{
+    if (!p || !out) return set_err(nullptr, LBM_ERR_ARG, "null argument");
+    Mapped m;
+    int rc = map_params(*p, m);
+    if (rc) return rc;
+    out[0] = m.Nf;
+    out[1] = m.omega;
+    out[2] = m.nuG;
+    out[3] = m.tau_s;
+    out[4] = m.tau_q;
+    out[5] = p->kappa;
+    return m.warn ? LBM_WARN_PR_RANGE : LBM_OK;
+}
+
+int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w)
+{
+    int cc[128][3];
+    double ww[128], rr;
+    int q = lbm::derive_lattice(lattice, cc, ww, &rr);
+    if (q < 0) return set_err(nullptr, LBM_ERR_ARG, "unknown lattice");
+    if (D) *D = lattice == LBM_D2Q37 ? 2 : 3;
+    if (Q) *Q = q;
+    if (r) *r = rr;
+    for (int i = 0; i < q; ++i) {
+        if (c)
+            for (int d = 0; d < 3; ++d) c[3 * i + d] = cc[i][d];
+        if (w) w[i] = ww[i];
+    }
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
+{
+    g_create_err.clear();
+    if (!pin || !out) return set_err(nullptr, LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    lbm_params p = *pin;
+    Mapped mp;
+    int rc = map_params(p, mp);
+    if (rc) return rc;
+    const int D = mp.D;
+    if (D == 2) p.nz = 1;
+    const double Nf = mp.Nf, omega = mp.omega, nuG = mp.nuG, tau_s = mp.tau_s, tau_q = mp.tau_q;
+    lbm_handle *h = new lbm_handle();
+    h->p = p;
+    h->D = D;
+    h->Q = lbm::derive_lattice(p.lattice, h->c, h->w, &h->r);
+    if (h->Q < 0) {
+        delete h;
+        return set_err(nullptr, LBM_ERR_ARG, "lattice derivation failed");
+    }
+    h->Nf = Nf;
+    h->omega = omega;
+    h->nuG = nuG;
+    h->tau_s = tau_s;
+    h->tau_q = tau_q;
+    h->stream = (cudaStream_t)stream;
+    lbm::Ctx &c = h->ctx;
+    memset(&c, 0, sizeof(c));
+    c.storage = p.storage;
+    c.walls = p.bc_y == LBM_WALLS;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.nz = p.nz;
+    c.gh = c.walls ? 2 : 0;
+    c.nys = p.ny + 2 * c.gh;
+    c.plane = (long long)p.nx * c.nys * p.nz;
+    c.omega = omega;
+    c.kappa = p.kappa;
+    c.a_tr = (1.0 - p.kappa) * (1.0 - nuG);
+    c.a_sig = (1.0 - p.kappa) * nuG;
+    c.Nf = Nf;
+    c.r = h->r;
+    for (int i = 0; i < h->Q; ++i) c.w[i] = h->w[i];
+    for (int b = 0; b < 2; ++b) {
+        for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
+        c.wall_T[b] = p.wall_T[b];
+    }
+    h->ops = D == 2 ? lbm::ops_d2q37(p.storage) : lbm::ops_d3q103(p.storage);
+    h->elem = p.storage == LBM_FP32 ? 4 : 2;
+    h->buf_elems = (size_t)2 * h->Q * (size_t)c.plane;
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(&h->buf[k], h->buf_elems * h->elem);
+        if (e != cudaSuccess) {
+            int code = set_err(nullptr, LBM_ERR_NOMEM, std::string("population buffer: ") + cudaGetErrorString(e));
+            if (k) cudaFree(h->buf[0]);
+            delete h;
+            return code;
+        }
+    }
+    const long long n = ncell(h);
+    h->diag_blocks = (int)std::min<long long>((n + lbm::kDiagThreads - 1) / lbm::kDiagThreads, 1216);
+    cudaError_t e = cudaMalloc(&h->d_partials, sizeof(double) * lbm::kDiagNV * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_out, sizeof(double) * lbm::kDiagNV);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_elems * h->elem, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->buf_elems * h->elem, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        int code = set_err(nullptr, LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+        lbm_destroy(h);
+        return code;
+    }
+    h->d_out = h->d_partials + (size_t)lbm::kDiagNV * h->diag_blocks;
+    *out = h;
+    if (nuG < -0.5) {
+        h->err = "Gaussian parameter nu < -1/2 (outside the paper's Pr range)";
+        return LBM_WARN_PR_RANGE;
+    }
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle *h)
+{
+    if (!h) return LBM_OK;
+    cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 2; ++k)
+        if (h->buf[k]) cudaFree(h->buf[k]);
+    if (h->d_partials) cudaFree(h->d_partials);
+    if (h->h_out) cudaFreeHost(h->h_out);
+    if (h->d_snap) cudaFree(h->d_snap);
+    if (h->d_stage) cudaFree(h->d_stage);
+    delete h;
+    return LBM_OK;
+}
+
+int lbm_lattice_info(const lbm_handle *h, int *D, int *Q, double *r, int *c, double *w)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (D) *D = h->D;
+    if (Q) *Q = h->Q;
+    if (r) *r = h->r;
+    for (int i = 0; i < h->Q; ++i) {
+        if (c)
+            for (int d = 0; d < 3; ++d) c[3 * i + d] = h->c[i][d];
+        if (w) w[i] = h->w[i];
+    }
+    return LBM_OK;
+}
+
+int lbm_coefficients(const lbm_handle *h, double *out)
+{
+    if (!h || !out) return LBM_ERR_ARG;
+    out[0] = h->Nf;
+    out[1] = h->omega;
+    out[2] = h->nuG;
+    out[3] = h->tau_s;
+    out[4] = h->tau_q;
+    out[5] = h->p.kappa;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const double *T, int mem)
+{
+    if (!h || !rho || !u || !T) return set_err(h, LBM_ERR_ARG, "null field");
+    const long long n = ncell(h);
+    const double *dr = rho, *du = u, *dT = T;
+    if (mem == LBM_MEM_HOST) {
+        int rc = ensure_stage(h, sizeof(double) * n * (h->D + 2));
+        if (rc) return rc;
+        double *s = h->d_stage;
+        LBM_CK(h, cudaMemcpyAsync(s, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        LBM_CK(h, cudaMemcpyAsync(s + n, u, sizeof(double) * n * h->D, cudaMemcpyHostToDevice, h->stream));
+        LBM_CK(h, cudaMemcpyAsync(s + n * (1 + h->D), T, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        dr = s;
+        du = s + n;
+        dT = s + n * (1 + h->D);
+    } else if (mem != LBM_MEM_DEVICE) {
+        return set_err(h, LBM_ERR_ARG, "bad mem");
+    }
+    h->ops.init(h->ctx, h->buf[h->cur], dr, du, dT, h->stream);
+    LBM_CK(h, cudaGetLastError());
+    h->steps = 0;
+    h->have_snap = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int nsteps)
+{
+    if (!h || nsteps < 0) return set_err(h, LBM_ERR_ARG, "bad nsteps");
+    for (int k = 0; k < nsteps; ++k) {
+        void *src = h->buf[h->cur], *dst = h->buf[h->cur ^ 1];
+        h->ops.step(h->ctx, src, dst, h->stream);
+        if (h->ctx.walls) h->ops.walls(h->ctx, dst, h->stream);
+        h->cur ^= 1;
+    }
+    h->steps += nsteps;
+    LBM_CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle *h, double *rho, double *u, double *T, double *Pi, double *q, int mem)
+{
+    if (!h) return LBM_ERR_ARG;
+    const long long n = ncell(h);
+    const int D = h->D, np = D * (D + 1) / 2;
+    if (mem == LBM_MEM_HOST) {
+        int rc = ensure_stage(h, sizeof(double) * n * (1 + D + 1 + np + D));
+        if (rc) return rc;
+        double *s = h->d_stage;
+        double *sr = s, *su = s + n, *sT = s + n * (1 + D), *sP = s + n * (2 + D), *sq = s + n * (2 + D + np);
+        h->ops.moments(h->ctx, h->buf[h->cur], rho ? sr : nullptr, u ? su : nullptr, T ? sT : nullptr,
+                       Pi ? sP : nullptr, q ? sq : nullptr, h->stream);
+        LBM_CK(h, cudaGetLastError());
+        if (rho) LBM_CK(h, cudaMemcpyAsync(rho, sr, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        if (u) LBM_CK(h, cudaMemcpyAsync(u, su, sizeof(double) * n * D, cudaMemcpyDeviceToHost, h->stream));
+        if (T) LBM_CK(h, cudaMemcpyAsync(T, sT, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        if (Pi) LBM_CK(h, cudaMemcpyAsync(Pi, sP, sizeof(double) * n * np, cudaMemcpyDeviceToHost, h->stream));
+        if (q) LBM_CK(h, cudaMemcpyAsync(q, sq, sizeof(double) * n * D, cudaMemcpyDeviceToHost, h->stream));
+    } else if (mem == LBM_MEM_DEVICE) {
+        h->ops.moments(h->ctx, h->buf[h->cur], rho, u, T, Pi, q, h->stream);
+        LBM_CK(h, cudaGetLastError());
+    } else {
+        return set_err(h, LBM_ERR_ARG, "bad mem");
+    }
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle *h, double *out)
+{
+    if (!h || !out) return set_err(h, LBM_ERR_ARG, "null argument");
+    const long long n = ncell(h);
+    if (!h->d_snap) LBM_CK(h, cudaMalloc(&h->d_snap, sizeof(float) * 2 * n));
+    h->ops.diag(h->ctx, h->buf[h->cur], h->d_snap, h->have_snap, h->d_partials, h->diag_blocks, h->stream);
+    lbm::launch_diag_final(h->d_partials, h->diag_blocks, h->d_out, h->stream);
+    LBM_CK(h, cudaGetLastError());
+    LBM_CK(h, cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double) * lbm::kDiagNV, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    const double *a = h->h_out;
+    out[0] = (double)n + a[0];
+    out[1] = a[1];
+    out[2] = a[2];
+    out[3] = h->D == 3 ? a[3] : 0.0;
+    out[4] = (double)n * 0.5 * (h->D + h->Nf) + a[4];
+    const long long m = h->steps - h->snap_step;
+    out[5] = 0.0;
+    if (h->have_snap && m > 0) {
+        double ru = a[6] > 0 ? std::sqrt(a[5] / a[6]) : 0.0;
+        double rT = a[8] > 0 ? std::sqrt(a[7] / a[8]) : 0.0;
+        out[5] = std::max(ru, rT) / (double)m;
+    }
+    out[6] = a[9];
+    out[7] = (double)h->steps;
+    h->have_snap = 1;
+    h->snap_step = h->steps;
+    if (a[9] > 0) return set_err(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density / temperature");
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle *h, double *g, double *hh, int mem)
+{
+    if (!h) return LBM_ERR_ARG;
+    const size_t bytes = sizeof(double) * (size_t)h->Q * (size_t)ncell(h);
+    if (mem == LBM_MEM_HOST) {
+        int rc = ensure_stage(h, 2 * bytes);
+        if (rc) return rc;
+        double *sg = h->d_stage, *sh = h->d_stage + bytes / sizeof(double);
+        h->ops.get_pops(h->ctx, h->buf[h->cur], sg, sh, h->stream);
+        LBM_CK(h, cudaGetLastError());
+        if (g) LBM_CK(h, cudaMemcpyAsync(g, sg, bytes, cudaMemcpyDeviceToHost, h->stream));
+        if (hh) LBM_CK(h, cudaMemcpyAsync(hh, sh, bytes, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        h->ops.get_pops(h->ctx, h->buf[h->cur], g, hh, h->stream);
+        LBM_CK(h, cudaGetLastError());
+    }
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle *h, const double *g, const double *hh, int mem)
+{
+    if (!h || !g || !hh) return set_err(h, LBM_ERR_ARG, "null argument");
+    const size_t bytes = sizeof(double) * (size_t)h->Q * (size_t)ncell(h);
+    const double *dg = g, *dh = hh;
+    if (mem == LBM_MEM_HOST) {
+        int rc = ensure_stage(h, 2 * bytes);
+        if (rc) return rc;
+        double *sg = h->d_stage, *sh = h->d_stage + bytes / sizeof(double);
+        LBM_CK(h, cudaMemcpyAsync(sg, g, bytes, cudaMemcpyHostToDevice, h->stream));
+        LBM_CK(h, cudaMemcpyAsync(sh, hh, bytes, cudaMemcpyHostToDevice, h->stream));
+        dg = sg;
+        dh = sh;
+    }
+    h->ops.set_pops(h->ctx, h->buf[h->cur], dg, dh, h->stream);
+    // ghost rows are a function of the domain rows: rebuild them
+    if (h->ctx.walls) h->ops.walls(h->ctx, h->buf[h->cur], h->stream);
+    LBM_CK(h, cudaGetLastError());
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+} // extern "C"

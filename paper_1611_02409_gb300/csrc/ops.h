@@ -1,0 +1,35 @@
+// Plain host-side interface between the C-ABI layer and the per-lattice kernel units.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+struct Ctx {
+    int storage, walls;
+    int nx, ny, nz, nys, gh;
+    long long plane;       // stored cells per population plane
+    double omega, kappa, a_tr, a_sig, Nf, r;
+    double w[128];
+    double wall_u[2][3], wall_T[2];
+};
+
+struct Ops {
+    void (*init)(const Ctx &, void *dst, const double *rho, const double *u, const double *T, cudaStream_t);
+    void (*step)(const Ctx &, const void *src, void *dst, cudaStream_t);
+    void (*walls)(const Ctx &, void *buf, cudaStream_t);
+    void (*moments)(const Ctx &, const void *buf, double *rho, double *u, double *T, double *Pi, double *q,
+                    cudaStream_t);
+    void (*diag)(const Ctx &, const void *buf, float *snap, int have_snap, double *partials, int nblk,
+                 cudaStream_t);
+    void (*get_pops)(const Ctx &, const void *buf, double *g, double *h, cudaStream_t);
+    void (*set_pops)(const Ctx &, void *buf, const double *g, const double *h, cudaStream_t);
+};
+
+Ops ops_d2q37(int storage);
+Ops ops_d3q103(int storage);
+void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);
+
+// FP64 lattice derivation (lattice_host.cu): fills c (Q x 3), w (Q) and r; returns Q or -1.
+int derive_lattice(int lattice, int (*c)[3], double *w, double *r);
+
+} // namespace lbm

@@ -1,0 +1,278 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``liblbm.so``; this module converts
+arguments, passes device pointers of torch tensors (or host numpy arrays) and
+raises on error codes.  There is no CPU fallback: if the library is missing the
+import of :func:`lib` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbm.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "lbm.h")
+
+LBM_OK = 0
+LBM_ERR_ARG = 1
+LBM_ERR_CUDA = 2
+LBM_ERR_UNSTABLE = 3
+LBM_ERR_NOMEM = 4
+LBM_WARN_PR_RANGE = 100
+LBM_D2Q37 = 1
+LBM_D3Q103 = 2
+LBM_PR_SHIFTED = 0
+LBM_PR_LITERAL = 1
+LBM_FP32 = 0
+LBM_FP16 = 1
+LBM_BF16 = 2
+LBM_PERIODIC = 0
+LBM_WALLS = 1
+LBM_MEM_DEVICE = 0
+LBM_MEM_HOST = 1
+
+STORAGE = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbm error {code}: {msg}")
+        self.code = code
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("Pr", C.c_double), ("gamma", C.c_double), ("N_f", C.c_double),
+                ("kappa", C.c_double), ("tau", C.c_double), ("pr_mode", C.c_int), ("storage", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc_y", C.c_int),
+                ("wall_u", (C.c_double * 3) * 2), ("wall_T", C.c_double * 2)]
+
+
+def make_params(lattice=LBM_D2Q37, Pr=0.71, gamma=1.4, N_f=0.0, kappa=0.2, tau=0.6, pr_mode=LBM_PR_SHIFTED,
+                storage=LBM_FP32, nx=64, ny=64, nz=1, bc_y=LBM_PERIODIC, wall_u=None, wall_T=None) -> lbm_params:
+    p = lbm_params()
+    p.lattice, p.Pr, p.gamma, p.N_f, p.kappa, p.tau = lattice, Pr, gamma, N_f, kappa, tau
+    p.pr_mode = pr_mode
+    p.storage = STORAGE.get(storage, storage) if isinstance(storage, str) else storage
+    p.nx, p.ny, p.nz, p.bc_y = nx, ny, nz, bc_y
+    wu = np.zeros((2, 3)) if wall_u is None else np.asarray(wall_u, float).reshape(2, 3)
+    wT = np.ones(2) if wall_T is None else np.asarray(wall_T, float).reshape(2)
+    for b in range(2):
+        for d in range(3):
+            p.wall_u[b][d] = wu[b, d]
+        p.wall_T[b] = wT[b]
+    return p
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def exported_names() -> list[str]:
+    """Entry points declared in include/lbm.h."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*|void)\s*\*?\s*(lbm_\w+)\s*\(", src, re.M)))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run paper_1611_02409_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+            L.lbm_create.argtypes = [C.POINTER(lbm_params), vp, C.POINTER(vp)]
+            L.lbm_destroy.argtypes = [vp]
+            L.lbm_last_error.argtypes = [vp]
+            L.lbm_last_error.restype = C.c_char_p
+            L.lbm_lattice_info.argtypes = [vp, ip, ip, dp, ip, dp]
+            L.lbm_lattice_table.argtypes = [C.c_int, ip, ip, dp, ip, dp]
+            L.lbm_map_params.argtypes = [C.POINTER(lbm_params), dp]
+            L.lbm_coefficients.argtypes = [vp, dp]
+            L.lbm_init_fields.argtypes = [vp, vp, vp, vp, C.c_int]
+            L.lbm_step.argtypes = [vp, C.c_int]
+            L.lbm_moments.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
+            L.lbm_diagnostics.argtypes = [vp, dp]
+            L.lbm_get_populations.argtypes = [vp, vp, vp, C.c_int]
+            L.lbm_set_populations.argtypes = [vp, vp, vp, C.c_int]
+            _lib = L
+    return _lib
+
+
+def lbm_last_error(h=None) -> str:
+    return lib().lbm_last_error(h).decode()
+
+
+def _check(code, h=None, warn_ok=False):
+    if code == LBM_OK or (warn_ok and code == LBM_WARN_PR_RANGE):
+        return code
+    raise LbmError(code, lbm_last_error(h))
+
+
+def lbm_lattice_table(lattice=LBM_D2Q37):
+    """(D, r, c[Q,3], w[Q]) as derived by the library's host code (no GPU needed)."""
+    D, Q, r = C.c_int(), C.c_int(), C.c_double()
+    c = np.zeros((128, 3), np.int32)
+    w = np.zeros(128)
+    _check(lib().lbm_lattice_table(lattice, C.byref(D), C.byref(Q), C.byref(r),
+                                   c.ctypes.data_as(C.POINTER(C.c_int)), w.ctypes.data_as(C.POINTER(C.c_double))))
+    return D.value, r.value, c[:Q.value].copy(), w[:Q.value].copy()
+
+
+def lbm_map_params(p: lbm_params) -> dict:
+    """Mapped coefficients of a parameter set (no GPU needed); raises on invalid sets."""
+    out = np.zeros(6)
+    code = lib().lbm_map_params(C.byref(p), out.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(code, None, warn_ok=True)
+    return dict(Nf=out[0], omega=out[1], nuG=out[2], tau_s=out[3], tau_q=out[4], kappa=out[5],
+                warn=code == LBM_WARN_PR_RANGE)
+
+
+def _ptr(x):
+    """(pointer, mem) of a torch CUDA tensor or a host numpy array (float64, contiguous)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):
+        if x.dtype.itemsize != 8 or not x.is_contiguous():
+            raise ValueError("fields must be contiguous float64")
+        return C.c_void_p(x.data_ptr()), (LBM_MEM_DEVICE if x.is_cuda else LBM_MEM_HOST)
+    if x.dtype != np.float64 or not x.flags.c_contiguous:
+        raise ValueError("fields must be contiguous float64")
+    return C.c_void_p(x.ctypes.data), LBM_MEM_HOST
+
+
+def _mem_of(*xs):
+    mems = {m for _, m in map(_ptr, xs) if m is not None}
+    if len(mems) != 1:
+        raise ValueError("all fields must live in the same memory space")
+    return mems.pop()
+
+
+def lbm_create(p: lbm_params, stream=None):
+    """Returns (handle, warn) with warn True for LBM_WARN_PR_RANGE."""
+    h = C.c_void_p()
+    s = C.c_void_p(stream) if isinstance(stream, int) else C.c_void_p(getattr(stream, "cuda_stream", 0) or 0)
+    code = lib().lbm_create(C.byref(p), s, C.byref(h))
+    _check(code, None, warn_ok=True)
+    return h, code == LBM_WARN_PR_RANGE
+
+
+def lbm_destroy(h):
+    return _check(lib().lbm_destroy(h), None)
+
+
+def lbm_init_fields(h, rho, u, T):
+    mem = _mem_of(rho, u, T)
+    return _check(lib().lbm_init_fields(h, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0], mem), h)
+
+
+def lbm_step(h, nsteps=1):
+    return _check(lib().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_moments(h, rho=None, u=None, T=None, Pi=None, q=None):
+    xs = [x for x in (rho, u, T, Pi, q) if x is not None]
+    mem = _mem_of(*xs) if xs else LBM_MEM_DEVICE
+    return _check(lib().lbm_moments(h, *(_ptr(x)[0] for x in (rho, u, T, Pi, q)), mem), h)
+
+
+def lbm_diagnostics(h, check=True):
+    out = np.zeros(8)
+    code = lib().lbm_diagnostics(h, out.ctypes.data_as(C.POINTER(C.c_double)))
+    if check:
+        _check(code, h)
+    return dict(mass=out[0], momentum=out[1:4].copy(), energy=out[4], residual=out[5], bad=int(out[6]),
+                steps=int(out[7]), code=code)
+
+
+def lbm_lattice_info(h):
+    D, Q, r = C.c_int(), C.c_int(), C.c_double()
+    c = np.zeros((128, 3), np.int32)
+    w = np.zeros(128)
+    _check(lib().lbm_lattice_info(h, C.byref(D), C.byref(Q), C.byref(r), c.ctypes.data_as(C.POINTER(C.c_int)),
+                                  w.ctypes.data_as(C.POINTER(C.c_double))), h)
+    return D.value, r.value, c[:Q.value].copy(), w[:Q.value].copy()
+
+
+def lbm_coefficients(h) -> dict:
+    out = np.zeros(6)
+    _check(lib().lbm_coefficients(h, out.ctypes.data_as(C.POINTER(C.c_double))), h)
+    return dict(Nf=out[0], omega=out[1], nuG=out[2], tau_s=out[3], tau_q=out[4], kappa=out[5])
+
+
+def lbm_get_populations(h, g, hh):
+    mem = _mem_of(g, hh)
+    return _check(lib().lbm_get_populations(h, _ptr(g)[0], _ptr(hh)[0], mem), h)
+
+
+def lbm_set_populations(h, g, hh):
+    mem = _mem_of(g, hh)
+    return _check(lib().lbm_set_populations(h, _ptr(g)[0], _ptr(hh)[0], mem), h)
+
+
+class Simulation:
+    """One handle with torch-allocated field tensors (device memory and stream only)."""
+
+    def __init__(self, stream=None, **kw):
+        import torch
+        self.torch = torch
+        self.p = make_params(**kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h, self.warn = lbm_create(self.p, self.stream)
+        self.D, self.r, self.c, self.w = lbm_lattice_info(self.h)
+        self.coeffs = lbm_coefficients(self.h)
+
+    @property
+    def shape(self):
+        p = self.p
+        return (p.nz, p.ny, p.nx) if self.D == 3 else (p.ny, p.nx)
+
+    def init(self, rho, u, T):
+        t = self.torch
+        dev = t.device("cuda")
+        f = lambda a: t.as_tensor(np.ascontiguousarray(a, np.float64), device=dev) \
+            if not hasattr(a, "data_ptr") else a.to(dev, t.float64).contiguous()
+        self._init_keep = (f(rho), f(u), f(T))
+        lbm_init_fields(self.h, *self._init_keep)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self, device=False):
+        t = self.torch
+        s, D = self.shape, self.D
+        out = dict(rho=t.empty(s, dtype=t.float64, device="cuda"), u=t.empty((D,) + s, dtype=t.float64, device="cuda"),
+                   T=t.empty(s, dtype=t.float64, device="cuda"),
+                   Pi=t.empty((D * (D + 1) // 2,) + s, dtype=t.float64, device="cuda"),
+                   q=t.empty((D,) + s, dtype=t.float64, device="cuda"))
+        lbm_moments(self.h, out["rho"], out["u"], out["T"], out["Pi"], out["q"])
+        return out if device else {k: v.cpu().numpy() for k, v in out.items()}
+
+    def diagnostics(self, check=True):
+        return lbm_diagnostics(self.h, check)
+
+    def populations(self):
+        Q = len(self.c)
+        g = np.zeros((Q,) + self.shape)
+        hh = np.zeros((Q,) + self.shape)
+        lbm_get_populations(self.h, g, hh)
+        return g, hh
+
+    def set_populations(self, g, hh):
+        lbm_set_populations(self.h, np.ascontiguousarray(g, np.float64), np.ascontiguousarray(hh, np.float64))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/lbm.h declares.  Host-only entry points (lattice derivation, parameter
+mapping) are checked against the oracle here; nothing launches a kernel."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1611_02409_gb300 import build
+    build.build()
+    from paper_1611_02409_gb300 import lbm
+    return lbm
+
+
+def test_exports_every_declared_symbol(L):
+    names = L.exported_names()
+    assert {"lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_destroy",
+            "lbm_diagnostics"} <= set(names)
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103)])
+def test_library_lattice_matches_oracle(L, lat, olat):
+    # two independent FP64 derivations of the same lattice must agree
+    D, r, c, w = L.lbm_lattice_table(lat)
+    Do, ro, co, wo = O.lattice(olat)
+    assert D == Do and len(c) == len(co)
+    assert abs(r - ro) < 1e-13
+    key = {tuple(v): wt for v, wt in zip(co, wo)}
+    for v, wt in zip(c, w):
+        assert wt == pytest.approx(key[tuple(v)], rel=1e-12)
+    # the library orders opposite velocities in adjacent pairs after the rest velocity
+    assert tuple(c[0]) == (0, 0, 0)
+    for k in range(1, len(c), 2):
+        assert tuple(c[k + 1]) == tuple(-c[k])
+
+
+@pytest.mark.parametrize("Pr,gamma,kappa,tau,mode", [(0.71, 1.4, 0.2, 0.528655, 0), (2.0, 1.3, 0.5, 1.0, 0),
+                                                      (0.5, 1.67, 0.2, 1.0, 0), (0.71, 1.4, 0.2, 0.8, 1)])
+def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
+    p = L.make_params(Pr=Pr, gamma=gamma, kappa=kappa, tau=tau, pr_mode=mode)
+    m = L.lbm_map_params(p)
+    o = O.params(2, Pr, gamma, 0.0, kappa, tau, mode)
+    for k in ("Nf", "omega", "nuG", "tau_s", "tau_q"):
+        assert m[k] == pytest.approx(o[k], rel=1e-13, abs=1e-15), k
+    assert m["warn"] == (m["nuG"] < -0.5)
+
+
+@pytest.mark.parametrize("bad", [dict(lattice=7), dict(tau=0.5), dict(Pr=0.0), dict(kappa=0.0), dict(kappa=1.2),
+                                 dict(gamma=2.5), dict(gamma=1.0), dict(nx=0), dict(bc_y=1, ny=4),
+                                 dict(lattice=2, bc_y=1), dict(storage=9), dict(pr_mode=4),
+                                 dict(kappa=1.0, Pr=0.71), dict(pr_mode=1, Pr=2.0, tau=0.9),
+                                 dict(bc_y=1, ny=16, wall_T=[1.0, -1.0])])
+def test_invalid_parameters_rejected_without_gpu(L, bad):
+    p = L.make_params(**bad)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_map_params(p)
+    assert e.value.code == L.LBM_ERR_ARG
+    # lbm_create rejects the same set before touching the device
+    h = C.c_void_p()
+    assert L.lib().lbm_create(C.byref(p), None, C.byref(h)) == L.LBM_ERR_ARG
+    assert not h.value
+    assert L.lbm_last_error()

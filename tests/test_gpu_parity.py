@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Error measures (the paper gives none): rel(X) = ||X_gpu - X_orc||_2 / ||X_orc||_2 per
+field, with u taken as one vector field; dev(X) = ||X_gpu - X_orc||_2 / ||X_orc - mean||_2
+normalises by the field's departure from its mean (the harder measure for rho and T).
+
+Tolerances:
+  * FP32 storage and arithmetic: rel <= 1e-5 (the required bar).  dev <= 1e-4: each step
+    rounds every stored deviation s ~ 1e-2 at 2^-24, and the conserved moments carry that
+    as a random walk, ~6e-8 * 1e-2 * sqrt(steps) per cell, i.e. ~2e-8 after 1000 steps
+    against field departures of 1e-3 (T) and 1e-2 (u): a few 1e-5 at most.
+  * FP16 storage (11-bit significand, 2^-11 relative rounding of s ~ 0.01-0.3): rel <= 1e-3.
+  * BF16 storage (8-bit significand, 8x coarser): rel <= 1e-2.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_02409_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1611_02409_gb300 import build
+    build.build()
+    from paper_1611_02409_gb300 import lbm
+    return lbm
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def dev(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b - b.mean())), 1e-300))
+
+
+def run_pair(L, fields, steps, storage="fp32", lattice=1, **kw):
+    """Same run on the GPU and on the oracle; returns both moment dicts."""
+    rho, u, T = fields
+    shape = rho.shape
+    D = len(shape)
+    nz, ny, nx = (shape if D == 3 else (1,) + shape)
+    sim = L.Simulation(lattice=lattice, nx=nx, ny=ny, nz=nz, storage=storage, **kw)
+    sim.init(rho, u, T)
+    sim.step(steps)
+    mg = sim.moments()
+    okw = {k: v for k, v in kw.items() if k not in ("bc_y",)}
+    if "pr_mode" in okw:
+        okw["mode"] = okw.pop("pr_mode")
+    o = O.Sim(O.D2Q37 if lattice == 1 else O.D3Q103, nx=nx, ny=ny, nz=nz,
+              walls=kw.get("bc_y", 0) == 1, **okw)
+    o.init(rho, u, T)
+    o.step(steps)
+    mo = o.moments()
+    sim.close()
+    return mg, mo, sim, o
+
+
+CFG0 = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
+
+
+def test_cfg0_periodic_64_fp32_1000_steps(L):
+    # 64 x 64 periodic D2Q37, shear wave + thermal wave + 1e-6 noise, 1000 steps
+    fields = inputs.shear_thermal_wave(64, 64, noise=1e-6, seed=0)
+    mg, mo, _, _ = run_pair(L, fields, 1000, **CFG0)
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= 1e-5, (k, rel(mg[k], mo[k]))
+        assert dev(mg[k], mo[k]) <= 1e-4, (k, dev(mg[k], mo[k]))
+    assert rel(mg["Pi"], mo["Pi"]) <= 1e-5
+
+
+def test_init_reproduces_fields(L):
+    fields = inputs.random_fields((23, 37), seed=3)
+    sim = L.Simulation(nx=37, ny=23, **CFG0)
+    sim.init(*fields)
+    m = sim.moments()
+    assert np.abs(m["rho"] - fields[0]).max() < 1e-6
+    assert np.abs(m["u"] - fields[1]).max() < 1e-6
+    assert np.abs(m["T"] - fields[2]).max() < 1e-6
+    sim.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(37, 23), (130, 9), (2, 7)])
+def test_populations_elementwise_ragged(L, nx, ny):
+    # several tiles plus a ragged tail (130 = 128 + 2), and the small-grid wrap path
+    fields = inputs.random_fields((ny, nx), seed=nx)
+    sim = L.Simulation(nx=nx, ny=ny, **CFG0)
+    sim.init(*fields)
+    o = O.Sim(O.D2Q37, nx=nx, ny=ny, **CFG0)
+    o.init(*fields)
+    for steps in (1, 9):
+        sim.step(steps)
+        o.step(steps)
+        gg, hg = sim.populations()
+        go, ho = o.populations()
+        # map the oracle's velocity order onto the library's
+        idx = [next(j for j in range(len(o.c)) if tuple(o.c[j]) == tuple(v)) for v in sim.c]
+        w = sim.w[:, None, None]
+        assert np.abs((gg - go[idx]) / w).max() < 2e-6
+        assert np.abs((hg - ho[idx]) / w).max() < 2e-6
+    sim.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 1e-2)])
+def test_low_precision_storage(L, storage, tol):
+    fields = inputs.taylor_green_2d(64, U0=0.02, T_amp=0.01)
+    mg, mo, _, _ = run_pair(L, fields, 200, storage=storage, **CFG0)
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= tol, (k, rel(mg[k], mo[k]))
+
+
+def test_walls_couette_parity(L):
+    wall = dict(bc_y=1, wall_u=[[0, 0, 0], [0.1, 0, 0]], wall_T=[1.0, 1.02])
+    fields = inputs.rest_channel(5, 33)
+    mg, mo, _, _ = run_pair(L, fields, 300, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8, **wall)
+    for k in ("rho", "T"):
+        assert rel(mg[k], mo[k]) <= 1e-5, (k, rel(mg[k], mo[k]))
+        assert dev(mg[k], mo[k]) <= 1e-4, (k, dev(mg[k], mo[k]))
+    assert rel(mg["u"], mo["u"]) <= 1e-5
+
+
+def test_walls_couette_analytic_profile(L):
+    # steady thermal Couette (Eq. CouetteDi3, unequal walls) on the GPU
+    Ny, U = 33, 0.2
+    sim = L.Simulation(nx=4, ny=Ny, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8, bc_y=1,
+                       wall_u=[[0, 0, 0], [U, 0, 0]], wall_T=[1.0, 1.01])
+    sim.init(*inputs.rest_channel(4, Ny))
+    sim.step(10000)
+    m = sim.moments()
+    yh = np.arange(Ny) / (Ny - 1)
+    heat = 0.71 * U ** 2 / (2 + sim.coeffs["Nf"] + 2)
+    Tan = 1.0 + 0.01 * yh + heat * yh * (1 - yh)
+    assert np.abs(m["u"][0].mean(1) - U * yh).max() < 1e-3 * U
+    assert np.abs(m["T"].mean(1) - Tan).max() < 0.1 * heat / 4
+    sim.close()
+
+
+def test_d3q103_parity(L):
+    fields = inputs.taylor_green_3d(12, U0=0.02, T_amp=0.01, noise=1e-6)
+    mg, mo, _, _ = run_pair(L, fields, 30, lattice=2, **CFG0)
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= 1e-5, (k, rel(mg[k], mo[k]))
+        assert dev(mg[k], mo[k]) <= 1e-4, (k, dev(mg[k], mo[k]))
+
+
+def test_nf_zero_and_literal_mode(L):
+    # N_f = 0 (gamma = (D+2)/D: no energy populations) and the paper-literal mapping
+    fields = inputs.shear_thermal_wave(16, 16, u_amp=0.02, T_amp=0.01, noise=0, seed=1)
+    mg, mo, _, _ = run_pair(L, fields, 50, Pr=1.0, gamma=2.0, kappa=0.3, tau=0.7)
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= 1e-5
+    mg, mo, _, _ = run_pair(L, fields, 50, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8, pr_mode=1)
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= 1e-5
+
+
+def test_diagnostics_conservation_and_residual(L):
+    fields = inputs.shear_thermal_wave(64, 64, seed=5)
+    sim = L.Simulation(nx=64, ny=64, **CFG0)
+    sim.init(*fields)
+    d0 = sim.diagnostics()
+    assert d0["residual"] == 0 and d0["bad"] == 0
+    o = O.Sim(O.D2Q37, nx=64, ny=64, **CFG0)
+    o.init(*fields)
+    e0 = o.diagnostics()
+    assert d0["mass"] == pytest.approx(e0["mass"], rel=1e-9)
+    assert d0["energy"] == pytest.approx(e0["energy"], rel=1e-9)
+    sim.step(200)
+    d1 = sim.diagnostics()
+    assert d1["steps"] == 200
+    assert abs(d1["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
+    assert abs(d1["energy"] - d0["energy"]) < 1e-6 * d0["energy"]
+    assert np.abs(d1["momentum"]).max() < 1e-6 * d0["mass"]
+    assert d1["residual"] > 0
+    sim.step(200)
+    d2 = sim.diagnostics()
+    assert 0 < d2["residual"] < d1["residual"]  # the waves decay
+    sim.close()
+
+
+def test_checkpoint_resume_bitwise(L):
+    fields = inputs.random_fields((20, 24), seed=11)
+    a = L.Simulation(nx=24, ny=20, **CFG0)
+    a.init(*fields)
+    a.step(5)
+    g, h = a.populations()
+    b = L.Simulation(nx=24, ny=20, **CFG0)
+    b.set_populations(g, h)
+    a.step(7)
+    b.step(7)
+    ga, ha = a.populations()
+    gb, hb = b.populations()
+    assert np.array_equal(ga, gb) and np.array_equal(ha, hb)
+    a.close()
+    b.close()
+
+
+def test_host_memory_fields_and_zero_steps(L):
+    fields = inputs.random_fields((16, 16), seed=2)
+    sim = L.Simulation(nx=16, ny=16, **CFG0)
+    L.lbm_init_fields(sim.h, *[np.ascontiguousarray(f) for f in fields])  # host pointers
+    sim.step(0)
+    rho = np.zeros((16, 16))
+    u = np.zeros((2, 16, 16))
+    T = np.zeros((16, 16))
+    L.lbm_moments(sim.h, rho, u, T)
+    assert np.abs(rho - fields[0]).max() < 1e-6 and np.abs(T - fields[2]).max() < 1e-6
+    sim.close()
+
+
+def test_full_size_sampled_one_step(L):
+    # 4096^2 thermal Taylor-Green in the benchmark's launch configuration: after one step,
+    # sampled cells against the oracle's collision of the streamed initial equilibria
+    import torch
+    n = 4096
+    rho, u, T = inputs.taylor_green_2d(n)
+    sim = L.Simulation(nx=n, ny=n, **CFG0)
+    sim.init(rho, u, T)
+    sim.step(1)
+    m = sim.moments(device=True)
+    o = O.Sim(O.D2Q37, nx=4, ny=4, **CFG0)
+    rng = np.random.default_rng(0)
+    pts = [(0, 0), (n - 1, n - 1), (1, n - 2)] + [tuple(rng.integers(0, n, 2)) for _ in range(29)]
+    Nf = o.coeffs["Nf"]
+    for (x, y) in pts:
+        g = np.zeros(len(o.c))
+        hh = np.zeros(len(o.c))
+        for i, cvec in enumerate(o.c):
+            xs, ys = (x - cvec[0]) % n, (y - cvec[1]) % n
+            G = O.equilibrium(O.D2Q37, rho[ys, xs], u[:, ys, xs], T[ys, xs] * np.eye(2))
+            g[i] = G[i]
+            hh[i] = 0.5 * Nf * T[ys, xs] * G[i]
+        go, ho = o.collide_cell(g, hh)
+        st = o.cell_state(go, ho)
+        assert abs(m["rho"][y, x].item() - st["rho"]) < 1e-6
+        assert np.abs(m["u"][:, y, x].cpu().numpy() - st["u"]).max() < 1e-7
+        assert abs(m["T"][y, x].item() - st["Teq"]) < 1e-6
+    del m
+    torch.cuda.synchronize()
+    sim.close()
