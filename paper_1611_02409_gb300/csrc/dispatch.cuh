@@ -24,7 +24,16 @@ template <int LAT> KParams<LAT> make_kparams(const Ctx &c)
     kp.Nf = (float)c.Nf;
     kp.halfNf = (float)(0.5 * c.Nf);
     kp.r = (float)c.r;
-    for (int i = 0; i < KParams<LAT>::Q; ++i) kp.w[i] = (float)c.w[i];
+    kp.r_d = c.r;
+    const double R2 = c.r * c.r;
+    kp.R2_hi = (float)R2;
+    kp.R2_lo = (float)(R2 - (double)kp.R2_hi);
+    for (int i = 0; i < KParams<LAT>::Q; ++i) {
+        kp.w[i] = (float)c.w[i];
+        const int sh = Lattice<LAT>::T.shell[i];
+        kp.wsh_hi[sh] = (float)c.w[i];
+        kp.wsh_lo[sh] = (float)(c.w[i] - (double)kp.wsh_hi[sh]);
+    }
     return kp;
 }
 
@@ -32,16 +41,16 @@ template <int LAT, int ST> struct Launch {
     using T = typename Storage<ST>::T;
     static constexpr int kTx = 128;
 
-    static dim3 rows_grid(const Ctx &c, int rows) { return dim3((c.nx + kTx - 1) / kTx, rows, c.nz); }
+    static dim3 rows_grid(const Ctx &c, int rows, int tx) { return dim3((c.nx + tx - 1) / tx, rows, c.nz); }
 
     static void init(const Ctx &c, void *dst, const double *rho, const double *u, const double *T_, cudaStream_t st)
     {
-        k_init<LAT, ST><<<rows_grid(c, c.nys), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_);
+        k_init<LAT, ST><<<rows_grid(c, c.nys, 64), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_);
     }
     static void step(const Ctx &c, const void *src, void *dst, cudaStream_t st)
     {
         const KParams<LAT> kp = make_kparams<LAT>(c);
-        const dim3 grid = rows_grid(c, kp.ny_comp);
+        const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
         const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
         if (c.walls)
             k_stream_collide<LAT, ST, true><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
@@ -53,7 +62,7 @@ template <int LAT, int ST> struct Launch {
         if constexpr (Lattice<LAT>::D == 2) {
             WallParams wp;
             for (int b = 0; b < 2; ++b) {
-                for (int d = 0; d < 3; ++d) wp.uw[b][d] = (float)c.wall_u[b][d];
+                for (int d = 0; d < 3; ++d) wp.vw[b][d] = (float)(c.wall_u[b][d] / c.r);
                 wp.thw[b] = (float)(c.wall_T[b] - 1.0);
             }
             k_walls<LAT, ST><<<dim3((c.nx + 63) / 64, 2, 1), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), wp);
@@ -62,7 +71,7 @@ template <int LAT, int ST> struct Launch {
     static void moments(const Ctx &c, const void *buf, double *rho, double *u, double *T_, double *Pi, double *q,
                         cudaStream_t st)
     {
-        k_moments<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), rho, u, T_,
+        k_moments<LAT, ST><<<rows_grid(c, c.ny, 64), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), rho, u, T_,
                                                              Pi, q);
     }
     static void diag(const Ctx &c, const void *buf, float *snap, int have_snap, double *partials, int nblk,
@@ -73,11 +82,11 @@ template <int LAT, int ST> struct Launch {
     }
     static void get_pops(const Ctx &c, const void *buf, double *g, double *h, cudaStream_t st)
     {
-        k_get_pops<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), g, h);
+        k_get_pops<LAT, ST><<<rows_grid(c, c.ny, 64), 64, 0, st>>>((const T *)buf, make_kparams<LAT>(c), g, h);
     }
     static void set_pops(const Ctx &c, void *buf, const double *g, const double *h, cudaStream_t st)
     {
-        k_set_pops<LAT, ST><<<rows_grid(c, c.ny), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), g, h);
+        k_set_pops<LAT, ST><<<rows_grid(c, c.ny, 64), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), g, h);
     }
 };
 

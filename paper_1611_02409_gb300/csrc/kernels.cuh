@@ -59,7 +59,7 @@ __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const floa
     EqState<D> e;
     es_state<LAT>(kp, c, e);
     PolyCoef<D> pc;
-    poly_coeffs<D>(e, kp.r, pc);
+    poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
     const EqScal z = eq_scalars<D>(e, kp.halfNf);
     relax_store<LAT, ST>(dst, o, kp.plane, 0, kp.omega, z, pc.k[0], s[0], t[0]);
     static_for<0, (Q - 1) / 2>([&](auto PP) {
@@ -107,17 +107,17 @@ __global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<S
     collide_store<LAT, ST>(kp, s, t, dst, o);
 }
 
-// Scaled equilibrium populations of (rho, u, T) with Lambda = T delta into s[], t[].
+// Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].
 template <int LAT>
-__device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho, const float (&u)[Lattice<LAT>::D],
+__device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho, const float (&v)[Lattice<LAT>::D],
                                              float th, float *s, float *t)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     EqState<D> e;
-    maxwell_state<D>(drho, u, th, e);
+    maxwell_state<D>(drho, v, kp.r, th, e);
     PolyCoef<D> pc;
-    poly_coeffs<D>(e, kp.r, pc);
+    poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
     const EqScal z = eq_scalars<D>(e, kp.halfNf);
     s[0] = fmaf(z.rho, pc.k[0], z.drho);
     t[0] = fmaf(z.hr, pc.k[0], z.hb);
@@ -148,11 +148,11 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<
     y = y < 0 ? 0 : (y > kp.ny - 1 ? kp.ny - 1 : y);
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
-    float uu[D];
+    float vv[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) uu[a] = (float)u[a * n + f];
+    for (int a = 0; a < D; ++a) vv[a] = (float)(u[a * n + f] / (double)kp.r_d);
     float s[Q], t[Q];
-    maxwell_pops<LAT>(kp, (float)(rho[f] - 1.0), uu, (float)(T[f] - 1.0), s, t);
+    maxwell_pops<LAT>(kp, (float)(rho[f] - 1.0), vv, (float)(T[f] - 1.0), s, t);
     const long long o = cell_index<LAT>(kp, x, ys, z);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -181,8 +181,8 @@ __device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restr
 // their Maxwellian).  rho_w balances exactly the mass the fluid sends into these rows
 // in the next streaming against the mass the rows send back.
 struct WallParams {
-    float uw[2][3];
-    float thw[2];   // T_w - 1
+    float vw[2][3];  // wall velocity in lattice units, u_w / r
+    float thw[2];    // T_w - 1
 };
 
 template <int LAT, int ST>
@@ -204,16 +204,16 @@ __global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams
     CellState<D> c;
     cell_state<LAT>(kp, m, c);
     float ms[Q], mt[Q];
-    maxwell_pops<LAT>(kp, c.drho, c.u, c.th_eq, ms, mt);
+    maxwell_pops<LAT>(kp, c.drho, c.v, c.th_eq, ms, mt);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {  // non-equilibrium of the first fluid row
         s1[i] -= ms[i];
         t1[i] -= mt[i];
     }
-    float uk[3][D], thk[3];
+    float uk[3][D], thk[3];   // lattice-unit velocities of the boundary rows
     for (int k = 0; k <= 2; ++k) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) uk[k][a] = wp.uw[b][a] - k * (c.u[a] - wp.uw[b][a]);
+        for (int a = 0; a < D; ++a) uk[k][a] = wp.vw[b][a] - k * (c.v[a] - wp.vw[b][a]);
         thk[k] = wp.thw[b] - k * (c.th_eq - wp.thw[b]);
     }
     // unit-density equilibria of the boundary rows (deviation / w): drho = 0

@@ -54,13 +54,22 @@ template <int LAT> struct KParams {
     float omega;          // relaxation rate
     float kappa, a_tr, a_sig; // Lambda = (1-k)[(1-nu) T_tr d + nu sigma] + k T_eq d
     float Nf, halfNf, r;
-    float w[Q];           // lattice weights
+    double r_d;           // r in FP64 (field input conversion)
+    float R2_hi, R2_lo;   // r^2 as an unevaluated float sum (hi + lo)
+    float w[Q];           // lattice weights (FP32), for the wall and flux sums
+    // Shell weights as hi + lo float pairs.  Conservation of momentum rests on the
+    // identity r^2 sum_i w_i c_i c_i = delta holding for the constants actually used:
+    // FP32-rounded r^2 and w_i miss it by ~1e-8, which the over-relaxed collision turns
+    // into a systematic drift j -> j (1 + omega eps) per step.  The moment sums therefore
+    // use w_hi + w_lo and the linear equilibrium term uses R2_hi + R2_lo.
+    float wsh_hi[Lattice<LAT>::NSHELL], wsh_lo[Lattice<LAT>::NSHELL];
 };
 
 // State that the equilibrium needs, in deviation form.
 template <int D> struct EqState {
     float drho, rho;      // rho - 1, rho
-    float u[D];
+    float u[D];           // velocity (xi units)
+    float v[D];           // velocity in lattice units, u / r
     float A[D][D];        // Lambda - delta
     float th_rel;         // T_rel - 1
 };
@@ -87,7 +96,8 @@ __device__ __forceinline__ float c4_of(const float (&A)[D][D], const float (&u)[
 }
 
 template <int D>
-__device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, PolyCoef<D> &pc)
+__device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float R2_hi, float R2_lo,
+                                            PolyCoef<D> &pc)
 {
     const auto &A = s.A;
     const auto &u = s.u;
@@ -117,10 +127,16 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, PolyCo
     // C_0 - 1 = -tr a2 / 2 + tr^2 a4 / 8
     const float c0 = -0.5f * (trA + u2)
                    + 0.125f * (trA * trA + 2.f * trA2 + 2.f * u2 * trA + 4.f * uAu + u2 * u2);
-    // C_1 = a1 - tr a3 / 2
-    float c1[D];
+    // r C_1 = r (a1 - tr a3 / 2) = r^2 y with y = v - (tr A v + 2 A v + u^2 v)/2, v = u/r
+    float k1[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) c1[a] = u[a] - 0.5f * (trA * u[a] + 2.f * Au[a] + u2 * u[a]);
+    for (int a = 0; a < D; ++a) {
+        float Av = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) Av += A[a][b] * s.v[b];
+        const float y = s.v[a] - 0.5f * (trA * s.v[a] + 2.f * Av + u2 * s.v[a]);
+        k1[a] = fmaf(R2_hi, y, R2_lo * y);
+    }
     // C_2 = a2 - tr a4 / 2
     float c2[D][D];
 #pragma unroll
@@ -130,7 +146,7 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, PolyCo
             c2[a][b] = A[a][b] + u[a] * u[b]
                      - 0.5f * (trA * A[a][b] + 2.f * A2[a][b] + trA * u[a] * u[b] + 2.f * Au[a] * u[b]
                                + 2.f * Au[b] * u[a] + u2 * A[a][b] + u2 * u[a] * u[b]);
-    const float r2 = r * r, r3 = r2 * r, r4 = r2 * r2;
+    const float r3 = R2_hi * r, r4 = R2_hi * R2_hi;
     static_for<0, PolyCoef<D>::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
         constexpr int m = Monos<D>::M.deg[K];
@@ -139,8 +155,12 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, PolyCo
         constexpr int i2 = mono_index<D, K>(2), i3 = mono_index<D, K>(3);
         float v;
         if constexpr (m == 0) v = c0;
-        else if constexpr (m == 1) v = r * c1[i0];
-        else if constexpr (m == 2) v = r2 * inv * c2[i0][i1];
+        else if constexpr (m == 1) v = k1[i0];
+        else if constexpr (m == 2) {
+            // leading even term: r^2 in hi + lo so that mass and energy sums close exactly
+            const float x = inv * c2[i0][i1];
+            v = fmaf(R2_hi, x, R2_lo * x);
+        }
         else if constexpr (m == 3) v = r3 * inv * c3_of<D>(A, u, i0, i1, i2);
         else v = r4 * inv * c4_of<D>(A, u, i0, i1, i2, i3);
         pc.k[K] = v;
@@ -186,48 +206,81 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float 
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
-    float drho = kp.w[0] * s[0], H = kp.w[0] * t[0];
-    float J[D], M[D][D];
+    constexpr int NM = 2 + D + D * (D + 1) / 2; // drho, H, J, M (upper triangle)
+    // hi and lo accumulators of the weighted sums
+    float hi[NM], lo[NM];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        J[a] = 0.f;
+    for (int k = 0; k < NM; ++k) hi[k] = lo[k] = 0.f;
+    // unweighted partial sums of the current shell (velocities come shell by shell)
+    float part[NM];
 #pragma unroll
-        for (int b = 0; b < D; ++b) M[a][b] = 0.f;
-    }
+    for (int k = 0; k < NM; ++k) part[k] = 0.f;
+    part[0] = s[0];
+    part[1] = t[0];
+    auto fold = [&](int sh) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+            hi[k] = fmaf(kp.wsh_hi[sh], part[k], hi[k]);
+            lo[k] = fmaf(kp.wsh_lo[sh], part[k], lo[k]);
+            part[k] = 0.f;
+        }
+    };
+    fold(0);
     // opposite pairs: the sum feeds the even moments, the difference the odd ones
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
-        const float w = kp.w[I];
-        const float ev = w * (s[I] + s[I + 1]);
-        const float od = w * (s[I] - s[I + 1]);
-        drho += ev;
-        H = fmaf(w, t[I] + t[I + 1], H);
+        constexpr int sh = Lattice<LAT>::T.shell[I];
+        const float ev = s[I] + s[I + 1];
+        const float od = s[I] - s[I + 1];
+        part[0] += ev;
+        part[1] += t[I] + t[I + 1];
+        int k = 2;
         static_for<0, D>([&](auto AA) {
             constexpr int a = decltype(AA)::value;
             constexpr int ca = cv<LAT, I, a>();
-            if constexpr (ca != 0) J[a] = fmaf((float)ca, od, J[a]);
+            if constexpr (ca == 1) part[2 + a] += od;
+            else if constexpr (ca == -1) part[2 + a] -= od;
+            else if constexpr (ca != 0) part[2 + a] = fmaf((float)ca, od, part[2 + a]);
+        });
+        k = 2 + D;
+        static_for<0, D>([&](auto AA) {
+            constexpr int a = decltype(AA)::value;
             static_for<a, D>([&](auto BB) {
                 constexpr int b = decltype(BB)::value;
-                constexpr int cab = ca * cv<LAT, I, b>();
-                if constexpr (cab != 0) M[a][b] = fmaf((float)cab, ev, M[a][b]);
+                constexpr int idx = 2 + D + a * D - a * (a - 1) / 2 + (b - a);
+                constexpr int cab = cv<LAT, I, a>() * cv<LAT, I, b>();
+                if constexpr (cab == 1) part[idx] += ev;
+                else if constexpr (cab == -1) part[idx] -= ev;
+                else if constexpr (cab != 0) part[idx] = fmaf((float)cab, ev, part[idx]);
             });
         });
+        (void)k;
+        constexpr bool last = (I + 2 >= Q) || (Lattice<LAT>::T.shell[I + 2] != sh);
+        if constexpr (last) fold(sh);
     });
-    m.drho = drho;
-    m.H = H;
+    float tot[NM];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        m.J[a] = J[a];
+    for (int k = 0; k < NM; ++k) tot[k] = hi[k] + lo[k];
+    m.drho = tot[0];
+    m.H = tot[1];
 #pragma unroll
-        for (int b = 0; b < D; ++b) m.M[a][b] = b >= a ? M[a][b] : M[b][a];
-    }
+    for (int a = 0; a < D; ++a) m.J[a] = tot[2 + a];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+            const float v = tot[2 + D + a * D - a * (a - 1) / 2 + (b - a)];
+            m.M[a][b] = v;
+            m.M[b][a] = v;
+        }
 }
 
 // Macroscopic state from raw moments: u, sigma - delta, theta = T - 1 for T_tr, T_int,
 // T_eq, T_rel, and Lambda - delta.
 template <int D> struct CellState {
     float drho, rho, inv_rho;
-    float u[D];
+    float v[D];           // lattice-unit velocity J / rho
+    float u[D];           // r v
     float sdev[D][D];     // sigma - delta
     float th_tr, th_int, th_eq, th_rel;
 };
@@ -240,15 +293,19 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
     c.drho = m.drho;
     c.rho = 1.f + m.drho;
     c.inv_rho = 1.f / c.rho;
-    const float r2 = kp.r * kp.r;
 #pragma unroll
-    for (int a = 0; a < D; ++a) c.u[a] = kp.r * m.J[a] * c.inv_rho;
+    for (int a = 0; a < D; ++a) {
+        c.v[a] = m.J[a] * c.inv_rho;
+        c.u[a] = kp.r * c.v[a];
+    }
     float tr = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) {
-            float v = (r2 * m.M[a][b] - (a == b ? m.drho : 0.f)) * c.inv_rho - c.u[a] * c.u[b];
+            // r^2 M in hi + lo: the temperature must see the same r^2 the energy sum uses
+            const float R2M = fmaf(kp.R2_hi, m.M[a][b], kp.R2_lo * m.M[a][b]);
+            float v = (R2M - (a == b ? m.drho : 0.f)) * c.inv_rho - c.u[a] * c.u[b];
             c.sdev[a][b] = v;
             if (a == b) tr += v;
         }
@@ -276,21 +333,23 @@ __device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         e.u[a] = c.u[a];
+        e.v[a] = c.v[a];
 #pragma unroll
         for (int b = 0; b < D; ++b) e.A[a][b] = kp.a_sig * c.sdev[a][b] + (a == b ? iso : 0.f);
     }
 }
 
-// Maxwellian state (Lambda = T delta) of (rho, u, T).
+// Maxwellian state (Lambda = T delta) of (rho, u = r v, T) given the lattice velocity v.
 template <int D>
-__device__ __forceinline__ void maxwell_state(float drho, const float (&u)[D], float th, EqState<D> &e)
+__device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], float r, float th, EqState<D> &e)
 {
     e.drho = drho;
     e.rho = 1.f + drho;
     e.th_rel = th;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        e.u[a] = u[a];
+        e.v[a] = v[a];
+        e.u[a] = r * v[a];
 #pragma unroll
         for (int b = 0; b < D; ++b) e.A[a][b] = a == b ? th : 0.f;
     }
