@@ -779,6 +779,26 @@ int orc_get_pops(void *p, double *g, double *h)
     return 0;
 }
 
+/* Sets the domain populations from SoA [i][z][y][x]; wall ghost rows are rebuilt by the
+ * wall procedure. */
+int orc_set_pops(void *p, const double *g, const double *h)
+{
+    orc_sim *S = p;
+    int Q = S->L.Q;
+    size_t ncell = (size_t)S->nx * S->ny * S->nz;
+    for (int z = 0; z < S->nz; ++z)
+        for (int y = 0; y < S->ny; ++y)
+            for (int x = 0; x < S->nx; ++x) {
+                size_t f = ((size_t)z * S->ny + y) * S->nx + x, c = orc_cell(S, x, y + S->gh, z);
+                for (int i = 0; i < Q; ++i) {
+                    S->g[c * Q + i] = g[i * ncell + f];
+                    S->h[c * Q + i] = h[i * ncell + f];
+                }
+            }
+    if (S->walls) orc_walls(S, S->g, S->h);
+    return 0;
+}
+
 long orc_steps(void *p) { return ((orc_sim *)p)->steps; }
 
 /* ------------------------------------------------------------------------- */

@@ -58,6 +58,7 @@ def lib():
             L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
             L.orc_diagnostics.argtypes = [C.c_void_p, dp]
             L.orc_get_pops.argtypes = [C.c_void_p, dp, dp]
+            L.orc_set_pops.argtypes = [C.c_void_p, dp, dp]
             L.orc_steps.argtypes = [C.c_void_p]
             L.orc_steps.restype = C.c_long
             L.orc_lattice_info.argtypes = [C.c_int, ip, ip, dp, ip, dp]
@@ -183,6 +184,10 @@ class Sim:
         g, h = np.zeros(Q * self.ncell), np.zeros(Q * self.ncell)
         self.L.orc_get_pops(self.h, _dp(g), _dp(h))
         return g.reshape((Q,) + self.shape), h.reshape((Q,) + self.shape)
+
+    def set_populations(self, g, h):
+        g, h = _f64(g), _f64(h)
+        self.L.orc_set_pops(self.h, _dp(g), _dp(h))
 
     def collide_cell(self, g, h):
         g, h = _f64(g), _f64(h)

@@ -39,7 +39,7 @@ __device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict_
                                             float q, float s, float t)
 {
     constexpr int Q = Lattice<LAT>::Q;
-    const float Gs = fmaf(z.rho, q, z.drho);
+    const float Gs = z.drho + q;
     const float Ht = fmaf(z.hr, q, z.hb);
     Storage<ST>::st(dst + (long long)I * plane + o, fmaf(om, Gs - s, s));
     Storage<ST>::st(dst + (long long)(Q + I) * plane + o, fmaf(om, Ht - t, t));
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<S
     if (x >= kp.nx) return;
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
-    float s[Q], t[Q];
+    typename S::Raw rs[Q], rt[Q];
     static_for<0, Q>([&](auto II) {
         constexpr int I = decltype(II)::value;
         constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
@@ -99,10 +99,18 @@ __global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<S
         int zs = z;
         if constexpr (D == 3) zs = wrap_sub<cz>(z, kp.nz, small_z);
         const long long idx = cell_index<LAT>(kp, xs, ys, zs);
-        s[I] = S::ld(src + (long long)I * kp.plane + idx);
-        t[I] = S::ld(src + (long long)(Q + I) * kp.plane + idx);
+        rs[I] = S::raw(src + (long long)I * kp.plane + idx);
+        rt[I] = S::raw(src + (long long)(Q + I) * kp.plane + idx);
     });
     (void)small_z;
+    // keep the conversions (and everything after) below the whole gather
+    asm volatile("" ::: "memory");
+    float s[Q], t[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        s[i] = S::cvt(rs[i]);
+        t[i] = S::cvt(rt[i]);
+    }
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
     collide_store<LAT, ST>(kp, s, t, dst, o);
 }
@@ -115,19 +123,19 @@ __device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho,
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     EqState<D> e;
-    maxwell_state<D>(drho, v, kp.r, th, e);
+    maxwell_state<D>(drho, v, kp.r, kp.R2_hi, th, e);
     PolyCoef<D> pc;
     poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
     const EqScal z = eq_scalars<D>(e, kp.halfNf);
-    s[0] = fmaf(z.rho, pc.k[0], z.drho);
+    s[0] = z.drho + pc.k[0];
     t[0] = fmaf(z.hr, pc.k[0], z.hb);
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
         float E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
-        s[I] = fmaf(z.rho, E + O, z.drho);
+        s[I] = z.drho + (E + O);
         t[I] = fmaf(z.hr, E + O, z.hb);
-        s[I + 1] = fmaf(z.rho, E - O, z.drho);
+        s[I + 1] = z.drho + (E - O);
         t[I + 1] = fmaf(z.hr, E - O, z.hb);
     });
 }
@@ -279,7 +287,7 @@ __global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const
         int k = 0;
         for (int a = 0; a < D; ++a)
             for (int bb = a; bb < D; ++bb)
-                Pi[(k++) * n + f] = (double)c.rho * ((a == bb ? 1.0 : 0.0) + (double)c.sdev[a][bb]);
+                Pi[(k++) * n + f] = (a == bb ? (double)c.rho : 0.0) + (double)c.rsdev[a][bb];
     }
     if (q) {
         // q_a = sum g |v|^2 v_a / 2 + sum h v_a, v = xi - u; the rest-state (w) part is

@@ -26,21 +26,38 @@ namespace lbm {
 
 enum : int { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
 
+// raw(): the stored bits, cvt(): to FP32.  The gather loads all raw values first and
+// converts them afterwards, so every load of a cell is in flight at once.
 template <int ST> struct Storage;
 template <> struct Storage<ST_FP32> {
     using T = float;
+    using Raw = float;
+    static __device__ __forceinline__ Raw raw(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ float cvt(Raw r) { return r; }
     static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
 };
 template <> struct Storage<ST_FP16> {
     using T = __half;
+    using Raw = unsigned short;
+    static __device__ __forceinline__ Raw raw(const T *p)
+    {
+        return __ldg(reinterpret_cast<const unsigned short *>(p));
+    }
+    static __device__ __forceinline__ float cvt(Raw r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ float ld(const T *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v))); }
 };
 template <> struct Storage<ST_BF16> {
     using T = __nv_bfloat16;
+    using Raw = unsigned short;
+    static __device__ __forceinline__ Raw raw(const T *p)
+    {
+        return __ldg(reinterpret_cast<const unsigned short *>(p));
+    }
+    static __device__ __forceinline__ float cvt(Raw r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
     static __device__ __forceinline__ float ld(const T *p) { return __bfloat162float(__ldg(p)); }
-    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v))); }
 };
 
 // Per-launch parameters (passed by value; read from the constant bank).
@@ -65,12 +82,18 @@ template <int LAT> struct KParams {
     float wsh_hi[Lattice<LAT>::NSHELL], wsh_lo[Lattice<LAT>::NSHELL];
 };
 
-// State that the equilibrium needs, in deviation form.
+// State that the equilibrium needs, in deviation form.  The leading (first-order) parts
+// are carried multiplied by rho (J = rho v, X = rho (A + u u), rho theta_rel) so that the
+// equilibrium's conserved moments come out of the lattice sums without a division by
+// rho: a rounded 1/rho is nearly the same in every cell of a smooth flow, and rho (1/rho)
+// != 1 would scale momentum by the same factor every step.
 template <int D> struct EqState {
-    float drho, rho;      // rho - 1, rho
-    float u[D];           // velocity (xi units)
-    float v[D];           // velocity in lattice units, u / r
-    float A[D][D];        // Lambda - delta
+    float drho, rho, inv_rho;
+    float J[D];           // rho v, v = u / r the lattice-unit velocity
+    float u[D];           // velocity (xi units), for second-order terms
+    float X[D][D];        // rho (A + u u), A = Lambda - delta
+    float A[D][D];        // A, for second-order terms
+    float rth_rel;        // rho (T_rel - 1)
     float th_rel;         // T_rel - 1
 };
 
@@ -95,22 +118,29 @@ __device__ __forceinline__ float c4_of(const float (&A)[D][D], const float (&u)[
          + u[a] * u[b] * u[c] * u[d];
 }
 
+// Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!.
 template <int D>
 __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float R2_hi, float R2_lo,
                                             PolyCoef<D> &pc)
 {
     const auto &A = s.A;
     const auto &u = s.u;
-    float trA = 0.f, u2 = 0.f, trA2 = 0.f, uAu = 0.f;
-    float Au[D], A2[D][D];
+    const float rho = s.rho;
+    float trA = 0.f, u2 = 0.f, trA2 = 0.f, uAu = 0.f, trX = 0.f;
+    float Au[D], AJ[D], A2[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         trA += A[a][a];
+        trX += s.X[a][a];
         u2 += u[a] * u[a];
-        float t = 0.f;
+        float t = 0.f, tj = 0.f;
 #pragma unroll
-        for (int b = 0; b < D; ++b) t += A[a][b] * u[b];
+        for (int b = 0; b < D; ++b) {
+            t += A[a][b] * u[b];
+            tj += A[a][b] * s.J[b];
+        }
         Au[a] = t;
+        AJ[a] = tj;
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -124,28 +154,24 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float 
             trA2 += A[a][b] * A[a][b];
         }
     }
-    // C_0 - 1 = -tr a2 / 2 + tr^2 a4 / 8
-    const float c0 = -0.5f * (trA + u2)
-                   + 0.125f * (trA * trA + 2.f * trA2 + 2.f * u2 * trA + 4.f * uAu + u2 * u2);
-    // r C_1 = r (a1 - tr a3 / 2) = r^2 y with y = v - (tr A v + 2 A v + u^2 v)/2, v = u/r
+    // rho (C_0 - 1) = -rho tr a2 / 2 + rho tr^2 a4 / 8,  rho tr a2 = tr X
+    const float k0 = -0.5f * trX + 0.125f * rho * (trA * trA + 2.f * trA2 + 2.f * u2 * trA + 4.f * uAu + u2 * u2);
+    // rho r C_1 = r^2 (J - (tr A J + 2 A J + u^2 J)/2)
     float k1[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        float Av = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) Av += A[a][b] * s.v[b];
-        const float y = s.v[a] - 0.5f * (trA * s.v[a] + 2.f * Av + u2 * s.v[a]);
+        const float y = s.J[a] - 0.5f * (trA * s.J[a] + 2.f * AJ[a] + u2 * s.J[a]);
         k1[a] = fmaf(R2_hi, y, R2_lo * y);
     }
-    // C_2 = a2 - tr a4 / 2
+    // rho C_2 = X - rho tr a4 / 2 (the trace part is second order)
     float c2[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b)
-            c2[a][b] = A[a][b] + u[a] * u[b]
-                     - 0.5f * (trA * A[a][b] + 2.f * A2[a][b] + trA * u[a] * u[b] + 2.f * Au[a] * u[b]
-                               + 2.f * Au[b] * u[a] + u2 * A[a][b] + u2 * u[a] * u[b]);
+            c2[a][b] = s.X[a][b]
+                     - 0.5f * rho * (trA * A[a][b] + 2.f * A2[a][b] + trA * u[a] * u[b] + 2.f * Au[a] * u[b]
+                                     + 2.f * Au[b] * u[a] + u2 * A[a][b] + u2 * u[a] * u[b]);
     const float r3 = R2_hi * r, r4 = R2_hi * R2_hi;
     static_for<0, PolyCoef<D>::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
@@ -154,15 +180,15 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float 
         constexpr int i0 = mono_index<D, K>(0), i1 = mono_index<D, K>(1);
         constexpr int i2 = mono_index<D, K>(2), i3 = mono_index<D, K>(3);
         float v;
-        if constexpr (m == 0) v = c0;
+        if constexpr (m == 0) v = k0;
         else if constexpr (m == 1) v = k1[i0];
         else if constexpr (m == 2) {
-            // leading even term: r^2 in hi + lo so that mass and energy sums close exactly
+            // r^2 in hi + lo so that the mass and energy sums close on the same constant
             const float x = inv * c2[i0][i1];
             v = fmaf(R2_hi, x, R2_lo * x);
         }
-        else if constexpr (m == 3) v = r3 * inv * c3_of<D>(A, u, i0, i1, i2);
-        else v = r4 * inv * c4_of<D>(A, u, i0, i1, i2, i3);
+        else if constexpr (m == 3) v = r3 * inv * rho * c3_of<D>(A, u, i0, i1, i2);
+        else v = r4 * inv * rho * c4_of<D>(A, u, i0, i1, i2, i3);
         pc.k[K] = v;
     });
 }
@@ -217,11 +243,28 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float 
     for (int k = 0; k < NM; ++k) part[k] = 0.f;
     part[0] = s[0];
     part[1] = t[0];
+    // Weighted fold of one shell's partial sums.  The momentum components (k = 2..D+1) fold
+    // error-free (TwoProduct + TwoSum into lo): their rounding on a smooth flow is coherent
+    // from cell to cell and from step to step, and the collision would inject it into the
+    // conserved momentum as a slow systematic drift.
     auto fold = [&](int sh) {
+        const float wh = kp.wsh_hi[sh], wl = kp.wsh_lo[sh];
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
-            hi[k] = fmaf(kp.wsh_hi[sh], part[k], hi[k]);
-            lo[k] = fmaf(kp.wsh_lo[sh], part[k], lo[k]);
+            if (k >= 2 && k < 2 + D) {
+                // _rn intrinsics: never contracted into FMAs, which would break the
+                // error-free transformations
+                const float p = __fmul_rn(wh, part[k]);
+                const float pe = fmaf(wh, part[k], -p);
+                const float sum = __fadd_rn(hi[k], p);
+                const float bv = __fsub_rn(sum, hi[k]);
+                const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(sum, bv)), __fsub_rn(p, bv));
+                hi[k] = sum;
+                lo[k] = fmaf(wl, part[k], lo[k] + (pe + e));
+            } else {
+                hi[k] = fmaf(wh, part[k], hi[k]);
+                lo[k] = fmaf(wl, part[k], lo[k]);
+            }
             part[k] = 0.f;
         }
     };
@@ -275,14 +318,17 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float 
         }
 }
 
-// Macroscopic state from raw moments: u, sigma - delta, theta = T - 1 for T_tr, T_int,
-// T_eq, T_rel, and Lambda - delta.
+// Macroscopic state from raw moments, rho-weighted: P = r^2 M - drho delta =
+// rho (sigma - delta) + rho u u, rho sdev = rho (sigma - delta), rho theta = rho (T - 1).
 template <int D> struct CellState {
     float drho, rho, inv_rho;
+    float J[D];           // rho v
     float v[D];           // lattice-unit velocity J / rho
     float u[D];           // r v
-    float sdev[D][D];     // sigma - delta
-    float th_tr, th_int, th_eq, th_rel;
+    float ruu[D][D];      // rho u u
+    float rsdev[D][D];    // rho (sigma - delta)
+    float rth_tr, rth_int, rth_eq, rth_rel;
+    float th_eq;          // T_eq - 1
 };
 
 template <int LAT>
@@ -295,6 +341,7 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
     c.inv_rho = 1.f / c.rho;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
+        c.J[a] = m.J[a];
         c.v[a] = m.J[a] * c.inv_rho;
         c.u[a] = kp.r * c.v[a];
     }
@@ -302,25 +349,34 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-            // r^2 M in hi + lo: the temperature must see the same r^2 the energy sum uses
+        for (int b = a; b < D; ++b) {
+            // r^2 M in hi + lo: the temperature sees the r^2 the energy sums use
             const float R2M = fmaf(kp.R2_hi, m.M[a][b], kp.R2_lo * m.M[a][b]);
-            float v = (R2M - (a == b ? m.drho : 0.f)) * c.inv_rho - c.u[a] * c.u[b];
-            c.sdev[a][b] = v;
+            const float ruu = kp.R2_hi * (c.J[a] * c.v[b]);
+            const float v = (R2M - (a == b ? m.drho : 0.f)) - ruu;
+            c.ruu[a][b] = c.ruu[b][a] = ruu;
+            c.rsdev[a][b] = c.rsdev[b][a] = v;
             if (a == b) tr += v;
         }
-    c.th_tr = tr * (1.f / D);
+    c.rth_tr = tr * (1.f / D);
     if (kp.Nf > 0.f) {
-        c.th_int = (2.f * m.H / kp.Nf - m.drho) * c.inv_rho;
-        c.th_eq = (D * c.th_tr + kp.Nf * c.th_int) / (D + kp.Nf);
-        c.th_rel = kp.kappa * c.th_eq + (1.f - kp.kappa) * c.th_int;
+        c.rth_int = 2.f * m.H / kp.Nf - m.drho;
+        c.rth_eq = (D * c.rth_tr + kp.Nf * c.rth_int) / (D + kp.Nf);
+        // T_rel = T_int + kappa (T_eq - T_int): equal to T_int at equilibrium whatever the
+        // rounding of kappa
+        c.rth_rel = fmaf(kp.kappa, c.rth_eq - c.rth_int, c.rth_int);
     } else {
-        c.th_int = 0.f;
-        c.th_eq = c.th_tr;
-        c.th_rel = c.th_tr;
+        c.rth_int = 0.f;
+        c.rth_eq = c.rth_tr;
+        c.rth_rel = c.rth_tr;
     }
+    c.th_eq = c.rth_eq * c.inv_rho;
 }
 
+// Lambda - delta = theta_tr delta + (1-kappa) nu (sigma - T_tr delta) + kappa (theta_eq - theta_tr) delta,
+// the same tensor as (1-kappa)[(1-nu) T_tr delta + nu sigma] + kappa T_eq delta - delta written so
+// that its trace, D theta_tr + kappa D (theta_eq - theta_tr), does not depend on rounded
+// complements of kappa (energy closes exactly in the collision).
 template <int LAT>
 __device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState<Lattice<LAT>::D> &c,
                                          EqState<Lattice<LAT>::D> &e)
@@ -328,46 +384,59 @@ __device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState
     constexpr int D = Lattice<LAT>::D;
     e.drho = c.drho;
     e.rho = c.rho;
-    e.th_rel = c.th_rel;
-    const float iso = kp.a_tr * c.th_tr + kp.kappa * c.th_eq;
+    e.inv_rho = c.inv_rho;
+    e.rth_rel = c.rth_rel;
+    e.th_rel = c.rth_rel * c.inv_rho;
+    const float iso = fmaf(kp.kappa, c.rth_eq - c.rth_tr, c.rth_tr);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
+        e.J[a] = c.J[a];
         e.u[a] = c.u[a];
-        e.v[a] = c.v[a];
 #pragma unroll
-        for (int b = 0; b < D; ++b) e.A[a][b] = kp.a_sig * c.sdev[a][b] + (a == b ? iso : 0.f);
+        for (int b = 0; b < D; ++b) {
+            const float rA = kp.a_sig * (c.rsdev[a][b] - (a == b ? c.rth_tr : 0.f)) + (a == b ? iso : 0.f);
+            e.X[a][b] = rA + c.ruu[a][b];
+            e.A[a][b] = rA * c.inv_rho;
+        }
     }
 }
 
 // Maxwellian state (Lambda = T delta) of (rho, u = r v, T) given the lattice velocity v.
 template <int D>
-__device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], float r, float th, EqState<D> &e)
+__device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], float r, float R2_hi, float th,
+                                              EqState<D> &e)
 {
     e.drho = drho;
     e.rho = 1.f + drho;
+    e.inv_rho = 1.f / e.rho;
     e.th_rel = th;
+    e.rth_rel = e.rho * th;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        e.v[a] = v[a];
+        e.J[a] = e.rho * v[a];
         e.u[a] = r * v[a];
-#pragma unroll
-        for (int b = 0; b < D; ++b) e.A[a][b] = a == b ? th : 0.f;
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            e.A[a][b] = a == b ? th : 0.f;
+            e.X[a][b] = (a == b ? e.rth_rel : 0.f) + R2_hi * (e.J[a] * v[b]);
+        }
 }
 
-// Scaled equilibrium deviations at velocity I given q_I:
-//   G~_I / w_I = drho + rho q,   H~_I / w_I = (N_f/2)(drho + rho th_rel + rho T_rel q)
+// Scaled equilibrium deviations at velocity I given Pq = rho q(c_I):
+//   G~_I / w_I = drho + Pq,   H~_I / w_I = (N_f/2)(drho + rho th_rel) + (N_f/2)(1 + th_rel) Pq
 struct EqScal {
-    float drho, rho, hb, hr; // hb = (N_f/2)(drho + rho th_rel), hr = (N_f/2) rho (1 + th_rel)
+    float drho, hb, hr;
 };
 
 template <int D> __device__ __forceinline__ EqScal eq_scalars(const EqState<D> &e, float halfNf)
 {
     EqScal z;
     z.drho = e.drho;
-    z.rho = e.rho;
-    z.hb = halfNf * fmaf(e.rho, e.th_rel, e.drho);
-    z.hr = halfNf * e.rho * (1.f + e.th_rel);
+    z.hb = halfNf * (e.drho + e.rth_rel);
+    z.hr = halfNf * (1.f + e.th_rel);
     return z;
 }
 
