@@ -37,6 +37,8 @@ extern "C" {
 #define LBM_ERR_CUDA 2       /* a CUDA call failed (text in lbm_last_error)         */
 #define LBM_ERR_UNSTABLE 3   /* non-finite or non-positive density / temperature    */
 #define LBM_ERR_NOMEM 4      /* device allocation failed                            */
+#define LBM_ERR_TIMEOUT 5    /* a bounded device-side wait gave up (the step's data
+                                are not valid); the context stays usable             */
 #define LBM_WARN_PR_RANGE 100 /* Gaussian parameter nu < -1/2: outside the paper's
                                 2/3 <= Pr bound for its literal mapping (Sec. III)  */
 
@@ -63,6 +65,12 @@ extern "C" {
 /* y boundaries */
 #define LBM_PERIODIC 0
 #define LBM_WALLS 1 /* hybrid kinetic (KBC) + non-equilibrium extrapolation walls (Sec. VI A) */
+
+/* stream-collide kernel variants (lbm_set_kernel / lbm_autotune) */
+#define LBM_KERNEL_AUTO 0    /* the library's default for the configuration            */
+#define LBM_KERNEL_DIRECT 1  /* one cell per thread, populations gathered from HBM     */
+#define LBM_KERNEL_STAGED 2  /* persistent tiles staged in shared memory by bulk
+                                asynchronous copies (D = 2, nx a multiple of 128)      */
 
 /* memory space of field pointers */
 #define LBM_MEM_DEVICE 0
@@ -138,6 +146,15 @@ int lbm_moments(lbm_handle *h, double *rho, double *u, double *T, double *Pi, do
  * a non-finite value, rho <= 0 or T <= 0; out[7] steps taken since lbm_init_fields.
  * Synchronises; returns LBM_ERR_UNSTABLE when out[6] > 0. */
 int lbm_diagnostics(lbm_handle *h, double *out);
+
+/* Selects the stream-collide kernel variant; LBM_ERR_ARG if the variant does not
+ * support this handle's configuration.  No paper counterpart: an implementation choice. */
+int lbm_set_kernel(lbm_handle *h, int variant);
+
+/* Times every admissible variant over `steps` steps (after 2 warm-up steps) on the
+ * handle's stream, selects the fastest and writes it to *chosen (may be NULL).  Resets
+ * the populations to the rest state (call before lbm_init_fields) and the step counter. */
+int lbm_autotune(lbm_handle *h, int steps, int *chosen);
 
 /* Checkpoint / resume: copies the domain populations (not ghost rows) as FP64 absolute
  * values g[Q][n], h[Q][n] (host or device per `mem`) out of / into the handle. */

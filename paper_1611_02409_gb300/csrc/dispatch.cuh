@@ -1,7 +1,9 @@
 // Host-side launch wrappers of the kernels for one lattice (included by one .cu per
 // lattice, which instantiates them and exports an Ops table to the C-ABI layer).
 #pragma once
-#include "kernels.cuh"
+#include <algorithm>
+
+#include "tma_kernel.cuh"
 #include "ops.h"
 
 namespace lbm {
@@ -33,6 +35,14 @@ template <int LAT> KParams<LAT> make_kparams(const Ctx &c)
         const int sh = Lattice<LAT>::T.shell[i];
         kp.wsh_hi[sh] = (float)c.w[i];
         kp.wsh_lo[sh] = (float)(c.w[i] - (double)kp.wsh_hi[sh]);
+        for (int d = 0; d < 3; ++d) kp.cvel[i][d] = (signed char)Lattice<LAT>::T.c[i][d];
+    }
+    const long long elem = c.storage == 0 ? 4 : 2;
+    for (int p = 0; p < 2 * KParams<LAT>::Q; ++p) {
+        const int i = p % KParams<LAT>::Q;
+        const long long cx = Lattice<LAT>::T.c[i][0], cy = Lattice<LAT>::T.c[i][1], cz = Lattice<LAT>::T.c[i][2];
+        kp.soff[p] = (long long)p * c.plane * elem;
+        kp.goff[p] = ((long long)p * c.plane - cz * (long long)c.nys * c.nx - cy * c.nx - cx) * elem;
     }
     return kp;
 }
@@ -47,9 +57,38 @@ template <int LAT, int ST> struct Launch {
     {
         k_init<LAT, ST><<<rows_grid(c, c.nys, 64), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_);
     }
+    // shared-memory-staged path: 2-D, nx a multiple of the tile width
+    static bool staged_ok(const Ctx &c)
+    {
+        return Lattice<LAT>::D == 2 && c.nx % TileGeom<ST>::TW == 0 && c.d_err != nullptr;
+    }
+    static bool tma_ok(const Ctx &c) { return c.kernel == 2 && staged_ok(c); }
+    template <bool W> static void step_tma(const Ctx &c, const KParams<LAT> &kp, const void *src, void *dst,
+                                           cudaStream_t st)
+    {
+        constexpr size_t smem = tma_smem_bytes<LAT, ST>();
+        static int blocks_per_sm = -1;
+        if (blocks_per_sm < 0) {
+            cudaFuncSetAttribute(k_stream_collide_tma<LAT, ST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_collide_tma<LAT, ST, W>, 128, smem);
+            blocks_per_sm = nb > 0 ? nb : 1;
+        }
+        const int ntiles = (c.nx / TileGeom<ST>::TW) * kp.ny_comp * c.nz;
+        const int grid = std::min(ntiles, blocks_per_sm * c.num_sms);
+        k_stream_collide_tma<LAT, ST, W><<<grid, 128, smem, st>>>((const T *)src, (T *)dst, kp, ntiles, c.d_err);
+    }
     static void step(const Ctx &c, const void *src, void *dst, cudaStream_t st)
     {
         const KParams<LAT> kp = make_kparams<LAT>(c);
+        if constexpr (Lattice<LAT>::D == 2) {
+            if (tma_ok(c)) {
+                if (c.walls) step_tma<true>(c, kp, src, dst, st);
+                else step_tma<false>(c, kp, src, dst, st);
+                return;
+            }
+        }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
         const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
         if (c.walls)
@@ -100,6 +139,7 @@ template <int LAT, int ST> Ops make_ops_st()
     o.diag = &Launch<LAT, ST>::diag;
     o.get_pops = &Launch<LAT, ST>::get_pops;
     o.set_pops = &Launch<LAT, ST>::set_pops;
+    o.staged_ok = &Launch<LAT, ST>::staged_ok;
     return o;
 }
 

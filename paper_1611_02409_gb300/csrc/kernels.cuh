@@ -32,42 +32,59 @@ __device__ __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, i
     return ((long long)z * kp.nys + ys) * kp.nx + x;
 }
 
-// Relax one opposite pair (I, I+1) and store it: s' = s + omega(G~/w - s), same for t.
+// Relax population I of a cell and store it: s' = s + omega(G~/w - s), same for t.
+// `cell` is the destination cell's address in set 0 plane 0; soff the planes' byte offsets.
 template <int LAT, int ST>
-__device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ dst, long long o,
-                                            long long plane, int I, float om, const EqScal &z,
-                                            float q, float s, float t)
+__device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ cell, const long long *soff,
+                                            int I, float om, const EqScal &z, float q, float s, float t)
 {
+    using T = typename Storage<ST>::T;
     constexpr int Q = Lattice<LAT>::Q;
-    const float Gs = z.drho + q;
-    const float Ht = fmaf(z.hr, q, z.hb);
-    Storage<ST>::st(dst + (long long)I * plane + o, fmaf(om, Gs - s, s));
-    Storage<ST>::st(dst + (long long)(Q + I) * plane + o, fmaf(om, Ht - t, t));
+    char *b = reinterpret_cast<char *>(cell);
+    if constexpr (ST == ST_FP32) {
+        // difference form: the non-equilibrium part G~/w - s is formed exactly
+        const float Gs = z.drho + q;
+        const float Ht = fmaf(z.hr, q, z.hb);
+        Storage<ST>::st(reinterpret_cast<T *>(b + soff[I]), fmaf(om, Gs - s, s));
+        Storage<ST>::st(reinterpret_cast<T *>(b + soff[Q + I]), fmaf(om, Ht - t, t));
+    } else {
+        // (1 - omega) s + omega G~/w in two FMAs (z carries omega-scaled terms); its extra
+        // FP32 rounding is far below the 16-bit storage rounding
+        Storage<ST>::st(reinterpret_cast<T *>(b + soff[I]), fmaf(z.om1, s, fmaf(om, q, z.wdrho)));
+        Storage<ST>::st(reinterpret_cast<T *>(b + soff[Q + I]), fmaf(z.om1, t, fmaf(z.whr, q, z.whb)));
+    }
 }
 
-// Collide the gathered populations s[], t[] of one cell and store them at offset o.
-template <int LAT, int ST>
-__device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const float *s, const float *t,
+// Collide one cell's streamed populations (accessor `pop`) and store them at offset o.
+template <int LAT, int ST, class Pop>
+__device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop &pop,
                                               typename Storage<ST>::T *__restrict__ dst, long long o)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
+    constexpr bool PRECISE = ST == ST_FP32;
     RawMoments<D> m;
-    raw_moments<LAT>(kp, s, t, m);
+    raw_moments<LAT, PRECISE>(kp, pop, m);
     CellState<D> c;
     cell_state<LAT>(kp, m, c);
     EqState<D> e;
     es_state<LAT>(kp, c, e);
     PolyCoef<D> pc;
-    poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
-    const EqScal z = eq_scalars<D>(e, kp.halfNf);
-    relax_store<LAT, ST>(dst, o, kp.plane, 0, kp.omega, z, pc.k[0], s[0], t[0]);
+    poly_coeffs<D>(e, kp.r, kp.R2_hi, PRECISE ? kp.R2_lo : 0.f, pc);
+    EqScal z = eq_scalars<D>(e, kp.halfNf);
+    z.om1 = 1.f - kp.omega;
+    z.wdrho = kp.omega * z.drho;
+    z.whb = kp.omega * z.hb;
+    z.whr = kp.omega * z.hr;
+    typename Storage<ST>::T *cell = dst + o;
+    relax_store<LAT, ST>(cell, kp.soff, 0, kp.omega, z, pc.k[0], pop.template sv<0>(), pop.template tv<0>());
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
         float E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
-        relax_store<LAT, ST>(dst, o, kp.plane, I, kp.omega, z, E + O, s[I], t[I]);
-        relax_store<LAT, ST>(dst, o, kp.plane, I + 1, kp.omega, z, E - O, s[I + 1], t[I + 1]);
+        relax_store<LAT, ST>(cell, kp.soff, I, kp.omega, z, E + O, pop.template sv<I>(), pop.template tv<I>());
+        relax_store<LAT, ST>(cell, kp.soff, I + 1, kp.omega, z, E - O, pop.template sv<I + 1>(),
+                             pop.template tv<I + 1>());
     });
 }
 
@@ -75,8 +92,12 @@ __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const floa
 // per cell of row y = y0 + blockIdx.y (plane z = blockIdx.z), all 2Q populations in
 // registers.  Periodic in x (and z, y when !WALLS); with WALLS the rows y - c_y reach
 // into the ghost rows, which the wall kernel filled after the previous step.
+// Four resident 128-thread blocks per SM (<= 128 registers) for the 2-D lattice: enough
+// loads in flight for FP32 and better latency hiding for the compute-bound 16-bit forms.
+template <int LAT, int ST> constexpr int direct_min_blocks() { return Lattice<LAT>::D == 2 ? 4 : 1; }
+
 template <int LAT, int ST, bool WALLS>
-__global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<ST>::T *__restrict__ src,
+__global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_collide(const typename Storage<ST>::T *__restrict__ src,
                                                         typename Storage<ST>::T *__restrict__ dst,
                                                         const KParams<LAT> kp, int small_x, int small_y,
                                                         int small_z)
@@ -84,24 +105,40 @@ __global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<S
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     using S = Storage<ST>;
+    using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
+    const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
+    // a block away from every periodic seam (|c| <= 3) gathers at fixed byte offsets
+    const int xb = blockIdx.x * blockDim.x;
+    bool interior = xb >= 3 && xb + (int)blockDim.x + 3 <= kp.nx;
+    if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
+    if constexpr (D == 3) interior = interior && z >= 3 && z + 3 < kp.nz;
     typename S::Raw rs[Q], rt[Q];
-    static_for<0, Q>([&](auto II) {
-        constexpr int I = decltype(II)::value;
-        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
-        const int xs = wrap_sub<cx>(x, kp.nx, small_x);
-        int ys;
-        if constexpr (WALLS) ys = y - cy + kp.gh;
-        else ys = wrap_sub<cy>(y, kp.ny, small_y);
-        int zs = z;
-        if constexpr (D == 3) zs = wrap_sub<cz>(z, kp.nz, small_z);
-        const long long idx = cell_index<LAT>(kp, xs, ys, zs);
-        rs[I] = S::raw(src + (long long)I * kp.plane + idx);
-        rt[I] = S::raw(src + (long long)(Q + I) * kp.plane + idx);
-    });
+    if (interior) {
+        const char *base = reinterpret_cast<const char *>(src + o);
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            rs[I] = S::raw(reinterpret_cast<const T *>(base + kp.goff[I]));
+            rt[I] = S::raw(reinterpret_cast<const T *>(base + kp.goff[Q + I]));
+        });
+    } else {
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
+            const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+            int ys;
+            if constexpr (WALLS) ys = y - cy + kp.gh;
+            else ys = wrap_sub<cy>(y, kp.ny, small_y);
+            int zs = z;
+            if constexpr (D == 3) zs = wrap_sub<cz>(z, kp.nz, small_z);
+            const long long idx = cell_index<LAT>(kp, xs, ys, zs);
+            rs[I] = S::raw(src + (long long)I * kp.plane + idx);
+            rt[I] = S::raw(src + (long long)(Q + I) * kp.plane + idx);
+        });
+    }
     (void)small_z;
     // keep the conversions (and everything after) below the whole gather
     asm volatile("" ::: "memory");
@@ -111,8 +148,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const typename Storage<S
         s[i] = S::cvt(rs[i]);
         t[i] = S::cvt(rt[i]);
     }
-    const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    collide_store<LAT, ST>(kp, s, t, dst, o);
+    collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o);
 }
 
 // Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].
@@ -208,7 +244,7 @@ __global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams
     float s1[Q], t1[Q];
     load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, yw + n + kp.gh, 0), s1, t1);
     RawMoments<D> m;
-    raw_moments<LAT>(kp, s1, t1, m);
+    raw_moments<LAT>(kp, ArrayPop{s1, t1}, m);
     CellState<D> c;
     cell_state<LAT>(kp, m, c);
     float ms[Q], mt[Q];
@@ -274,7 +310,7 @@ __global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const
     float s[Q], t[Q];
     load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
     RawMoments<D> m;
-    raw_moments<LAT>(kp, s, t, m);
+    raw_moments<LAT>(kp, ArrayPop{s, t}, m);
     CellState<D> c;
     cell_state<LAT>(kp, m, c);
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
@@ -363,7 +399,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const typename Storage<ST
         float s[Q], t[Q];
         load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
         RawMoments<D> m;
-        raw_moments<LAT>(kp, s, t, m);
+        raw_moments<LAT>(kp, ArrayPop{s, t}, m);
         CellState<D> c;
         cell_state<LAT>(kp, m, c);
         acc[0] += (double)m.drho;

@@ -34,6 +34,7 @@ struct lbm_handle {
     float *d_snap;         // u_x and T - 1 of the previous diagnostics call
     int have_snap;
     long long snap_step;
+    int *d_err;            // device error word of the kernels' bounded waits
     double *d_stage;       // device staging for host-memory field I/O
     size_t stage_bytes;
     std::string err;
@@ -242,7 +243,14 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
     }
     const long long n = ncell(h);
     h->diag_blocks = (int)std::min<long long>((n + lbm::kDiagThreads - 1) / lbm::kDiagThreads, 1216);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    h->ctx.kernel = LBM_KERNEL_DIRECT;
     cudaError_t e = cudaMalloc(&h->d_partials, sizeof(double) * lbm::kDiagNV * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) h->ctx.d_err = h->d_err;
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_out, sizeof(double) * lbm::kDiagNV);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_elems * h->elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->buf_elems * h->elem, h->stream);
@@ -268,6 +276,7 @@ int lbm_destroy(lbm_handle *h)
     for (int k = 0; k < 2; ++k)
         if (h->buf[k]) cudaFree(h->buf[k]);
     if (h->d_partials) cudaFree(h->d_partials);
+    if (h->d_err) cudaFree(h->d_err);
     if (h->h_out) cudaFreeHost(h->h_out);
     if (h->d_snap) cudaFree(h->d_snap);
     if (h->d_stage) cudaFree(h->d_stage);
@@ -340,6 +349,18 @@ int lbm_step(lbm_handle *h, int nsteps)
     return LBM_OK;
 }
 
+// Reads the device error word after a synchronisation; clears it.
+static int check_device_error(lbm_handle *h)
+{
+    int v = 0;
+    LBM_CK(h, cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) {
+        LBM_CK(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        return set_err(h, LBM_ERR_TIMEOUT, "a device-side wait gave up; results of the affected steps are invalid");
+    }
+    return LBM_OK;
+}
+
 int lbm_moments(lbm_handle *h, double *rho, double *u, double *T, double *Pi, double *q, int mem)
 {
     if (!h) return LBM_ERR_ARG;
@@ -365,7 +386,7 @@ int lbm_moments(lbm_handle *h, double *rho, double *u, double *T, double *Pi, do
         return set_err(h, LBM_ERR_ARG, "bad mem");
     }
     LBM_CK(h, cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_device_error(h);
 }
 
 int lbm_diagnostics(lbm_handle *h, double *out)
@@ -378,6 +399,10 @@ int lbm_diagnostics(lbm_handle *h, double *out)
     LBM_CK(h, cudaGetLastError());
     LBM_CK(h, cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double) * lbm::kDiagNV, cudaMemcpyDeviceToHost, h->stream));
     LBM_CK(h, cudaStreamSynchronize(h->stream));
+    {
+        int rc = check_device_error(h);
+        if (rc) return rc;
+    }
     const double *a = h->h_out;
     out[0] = (double)n + a[0];
     out[1] = a[1];
@@ -396,6 +421,58 @@ int lbm_diagnostics(lbm_handle *h, double *out)
     h->have_snap = 1;
     h->snap_step = h->steps;
     if (a[9] > 0) return set_err(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density / temperature");
+    return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_handle *h, int variant)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (variant == LBM_KERNEL_AUTO) variant = LBM_KERNEL_DIRECT;
+    if (variant == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx))
+        return set_err(h, LBM_ERR_ARG, "staged kernel needs D = 2 and nx a multiple of 128");
+    if (variant != LBM_KERNEL_DIRECT && variant != LBM_KERNEL_STAGED) return set_err(h, LBM_ERR_ARG, "bad variant");
+    h->ctx.kernel = variant;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle *h, int steps, int *chosen)
+{
+    if (!h || steps < 1) return set_err(h, LBM_ERR_ARG, "bad arguments");
+    cudaEvent_t e0, e1;
+    LBM_CK(h, cudaEventCreate(&e0));
+    LBM_CK(h, cudaEventCreate(&e1));
+    float best = -1.f;
+    int best_v = LBM_KERNEL_DIRECT;
+    for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_STAGED; ++v) {
+        if (v == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx)) continue;
+        h->ctx.kernel = v;
+        int rc = lbm_step(h, 2);
+        if (rc) return rc;
+        LBM_CK(h, cudaEventRecord(e0, h->stream));
+        rc = lbm_step(h, steps);
+        if (rc) return rc;
+        LBM_CK(h, cudaEventRecord(e1, h->stream));
+        LBM_CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LBM_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        if (best < 0 || ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        int rc = check_device_error(h);
+        if (rc) return rc;
+    }
+    h->ctx.kernel = best_v;
+    LBM_CK(h, cudaMemsetAsync(h->buf[0], 0, h->buf_elems * h->elem, h->stream));
+    LBM_CK(h, cudaMemsetAsync(h->buf[1], 0, h->buf_elems * h->elem, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
+    h->steps = 0;
+    h->have_snap = 0;
+    if (chosen) *chosen = best_v;
     return LBM_OK;
 }
 

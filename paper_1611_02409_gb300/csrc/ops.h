@@ -11,6 +11,9 @@ struct Ctx {
     double omega, kappa, a_tr, a_sig, Nf, r;
     double w[128];
     double wall_u[2][3], wall_T[2];
+    int *d_err;            // device error word (bounded waits that gave up set it)
+    int num_sms;
+    int kernel;            // 1 direct, 2 shared-memory staged
 };
 
 struct Ops {
@@ -23,6 +26,7 @@ struct Ops {
                  cudaStream_t);
     void (*get_pops)(const Ctx &, const void *buf, double *g, double *h, cudaStream_t);
     void (*set_pops)(const Ctx &, void *buf, const double *g, const double *h, cudaStream_t);
+    bool (*staged_ok)(const Ctx &);
 };
 
 Ops ops_d2q37(int storage);

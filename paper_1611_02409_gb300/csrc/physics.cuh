@@ -80,6 +80,11 @@ template <int LAT> struct KParams {
     // into a systematic drift j -> j (1 + omega eps) per step.  The moment sums therefore
     // use w_hi + w_lo and the linear equilibrium term uses R2_hi + R2_lo.
     float wsh_hi[Lattice<LAT>::NSHELL], wsh_lo[Lattice<LAT>::NSHELL];
+    signed char cvel[Q][3]; // integer velocities, for runtime-indexed loops
+    // Byte offsets, relative to a cell's own address in set 0 plane 0, of the source of
+    // population p (p < Q: g_p, else h_{p-Q}) for a cell away from the periodic seams,
+    // and of its destination; the gather then needs no per-population index arithmetic.
+    long long goff[2 * Q], soff[2 * Q];
 };
 
 // State that the equilibrium needs, in deviation form.  The leading (first-order) parts
@@ -226,9 +231,19 @@ template <int D> struct RawMoments {
     float H;              // sum h~
 };
 
-template <int LAT>
-__device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float *s, const float *t,
-                                            RawMoments<Lattice<LAT>::D> &m)
+// Population accessors: pop.template sv<I>() / tv<I>() return the scaled deviations s_I,
+// t_I of one cell (from registers, or from a shared-memory tile).
+struct ArrayPop {
+    const float *s, *t;
+    template <int I> __device__ __forceinline__ float sv() const { return s[I]; }
+    template <int I> __device__ __forceinline__ float tv() const { return t[I]; }
+};
+
+// PRECISE (FP32 storage): hi + lo shell weights and an error-free momentum fold.  The
+// 16-bit storage forms round every population to 2^-11 (FP16) or 2^-8 (BF16) each step,
+// far above these 1e-8 effects, and fold with the FP32 weights alone.
+template <int LAT, bool PRECISE = true, class Pop>
+__device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &pop, RawMoments<Lattice<LAT>::D> &m)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
@@ -241,14 +256,22 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float 
     float part[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) part[k] = 0.f;
-    part[0] = s[0];
-    part[1] = t[0];
+    part[0] = pop.template sv<0>();
+    part[1] = pop.template tv<0>();
     // Weighted fold of one shell's partial sums.  The momentum components (k = 2..D+1) fold
     // error-free (TwoProduct + TwoSum into lo): their rounding on a smooth flow is coherent
     // from cell to cell and from step to step, and the collision would inject it into the
     // conserved momentum as a slow systematic drift.
     auto fold = [&](int sh) {
         const float wh = kp.wsh_hi[sh], wl = kp.wsh_lo[sh];
+        if constexpr (!PRECISE) {
+#pragma unroll
+            for (int k = 0; k < NM; ++k) {
+                hi[k] = fmaf(wh, part[k], hi[k]);
+                part[k] = 0.f;
+            }
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
             if (k >= 2 && k < 2 + D) {
@@ -273,10 +296,11 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const float 
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
         constexpr int sh = Lattice<LAT>::T.shell[I];
-        const float ev = s[I] + s[I + 1];
-        const float od = s[I] - s[I + 1];
+        const float sa = pop.template sv<I>(), sb = pop.template sv<I + 1>();
+        const float ev = sa + sb;
+        const float od = sa - sb;
         part[0] += ev;
-        part[1] += t[I] + t[I + 1];
+        part[1] += pop.template tv<I>() + pop.template tv<I + 1>();
         int k = 2;
         static_for<0, D>([&](auto AA) {
             constexpr int a = decltype(AA)::value;
@@ -429,6 +453,7 @@ __device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], f
 //   G~_I / w_I = drho + Pq,   H~_I / w_I = (N_f/2)(drho + rho th_rel) + (N_f/2)(1 + th_rel) Pq
 struct EqScal {
     float drho, hb, hr;
+    float om1, wdrho, whb, whr; // 1 - omega and omega-scaled terms (16-bit storage relaxation)
 };
 
 template <int D> __device__ __forceinline__ EqScal eq_scalars(const EqState<D> &e, float halfNf)

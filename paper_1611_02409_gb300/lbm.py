@@ -23,6 +23,7 @@ LBM_ERR_ARG = 1
 LBM_ERR_CUDA = 2
 LBM_ERR_UNSTABLE = 3
 LBM_ERR_NOMEM = 4
+LBM_ERR_TIMEOUT = 5
 LBM_WARN_PR_RANGE = 100
 LBM_D2Q37 = 1
 LBM_D3Q103 = 2
@@ -33,6 +34,9 @@ LBM_FP16 = 1
 LBM_BF16 = 2
 LBM_PERIODIC = 0
 LBM_WALLS = 1
+LBM_KERNEL_AUTO = 0
+LBM_KERNEL_DIRECT = 1
+LBM_KERNEL_STAGED = 2
 LBM_MEM_DEVICE = 0
 LBM_MEM_HOST = 1
 
@@ -100,6 +104,8 @@ def lib():
             L.lbm_diagnostics.argtypes = [vp, dp]
             L.lbm_get_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_populations.argtypes = [vp, vp, vp, C.c_int]
+            L.lbm_set_kernel.argtypes = [vp, C.c_int]
+            L.lbm_autotune.argtypes = [vp, C.c_int, ip]
             _lib = L
     return _lib
 
@@ -205,6 +211,16 @@ def lbm_coefficients(h) -> dict:
     return dict(Nf=out[0], omega=out[1], nuG=out[2], tau_s=out[3], tau_q=out[4], kappa=out[5])
 
 
+def lbm_set_kernel(h, variant):
+    return _check(lib().lbm_set_kernel(h, int(variant)), h)
+
+
+def lbm_autotune(h, steps=10) -> int:
+    chosen = C.c_int()
+    _check(lib().lbm_autotune(h, int(steps), C.byref(chosen)), h)
+    return chosen.value
+
+
 def lbm_get_populations(h, g, hh):
     mem = _mem_of(g, hh)
     return _check(lib().lbm_get_populations(h, _ptr(g)[0], _ptr(hh)[0], mem), h)
@@ -218,12 +234,14 @@ def lbm_set_populations(h, g, hh):
 class Simulation:
     """One handle with torch-allocated field tensors (device memory and stream only)."""
 
-    def __init__(self, stream=None, **kw):
+    def __init__(self, stream=None, kernel=LBM_KERNEL_AUTO, **kw):
         import torch
         self.torch = torch
         self.p = make_params(**kw)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.h, self.warn = lbm_create(self.p, self.stream)
+        if kernel != LBM_KERNEL_AUTO:
+            lbm_set_kernel(self.h, kernel)
         self.D, self.r, self.c, self.w = lbm_lattice_info(self.h)
         self.coeffs = lbm_coefficients(self.h)
 

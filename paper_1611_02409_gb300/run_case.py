@@ -20,13 +20,15 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "staged"])
     a = ap.parse_args()
     import torch
 
     from paper_1611_02409_gb300 import build, inputs, lbm
     build.build()
     n = a.grid
-    params = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655, storage=a.storage)
+    params = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655, storage=a.storage,
+                  kernel={"auto": 0, "direct": 1, "staged": 2}[a.kernel])
     if a.lattice == "d2q37":
         sim = lbm.Simulation(lattice=lbm.LBM_D2Q37, nx=n, ny=n, **params)
         fields = inputs.taylor_green_2d(n)
@@ -47,7 +49,7 @@ def main():
     ms = e0.elapsed_time(e1) / a.steps
     d = sim.diagnostics()
     sim.close()
-    print(json.dumps({"lattice": a.lattice, "grid": n, "storage": a.storage, "steps": a.steps,
+    print(json.dumps({"lattice": a.lattice, "grid": n, "storage": a.storage, "kernel": a.kernel, "steps": a.steps,
                       "ms_per_step": ms, "mlups": cells / (ms * 1e-3) / 1e6, "bad_cells": d["bad"]}))
     if d["bad"]:
         raise SystemExit("non-finite state")
