@@ -156,6 +156,26 @@ int lbm_set_kernel(lbm_handle *h, int variant);
  * the populations to the rest state (call before lbm_init_fields) and the step counter. */
 int lbm_autotune(lbm_handle *h, int steps, int *chosen);
 
+/* Conservation totals of caller-owned FP64 device fields, allocating nothing (the paper
+ * has no counterpart: this serves callers that cannot call cudaMalloc, for instance code
+ * whose device memory was all reserved up front by a host framework, or a time-critical
+ * loop that must not risk the device synchronisation an allocation can bring).
+ *   rho[n], u[D][n], T[n]: device arrays in the field layout above (e.g. lbm_moments
+ *     output); out: device array of 6 doubles receiving sum rho, sum rho u_x, _y, _z
+ *     (0 for D = 2), sum rho (u^2/2 + (D + N_f) T / 2) and the number of cells with a
+ *     non-finite value, rho <= 0 or T <= 0.  N_f as lbm_coefficients reports it.
+ *   Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream); the call
+ *   does not synchronise.  Limit: n <= 33,554,432 cells, else LBM_ERR_ARG.
+ * The block partial sums live in one fixed 96 KiB __device__ array inside the library,
+ * held on every GPU that loads it until the process exits.  The first call on each
+ * device looks that array's address up (cudaGetSymbolAddress) with the device current,
+ * so make a first call on each device before any stream capture.  Every call shares the
+ * array and its last contents; each call overwrites the rows it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams, other threads) race on it.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA; text in lbm_last_error(NULL). */
+int lbm_field_totals_static(int D, double N_f, long long n, const double *rho, const double *u, const double *T,
+                            double *out, void *stream);
+
 /* Checkpoint / resume: copies the domain populations (not ghost rows) as FP64 absolute
  * values g[Q][n], h[Q][n] (host or device per `mem`) out of / into the handle. */
 int lbm_get_populations(lbm_handle *h, double *g, double *hh, int mem);

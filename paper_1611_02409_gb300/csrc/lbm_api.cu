@@ -95,6 +95,8 @@ void launch_diag_final(const double *partials, int nblk, double *out, cudaStream
 {
     k_diag_final<<<1, kDiagThreads, 0, st>>>(partials, nblk, out);
 }
+
+int set_global_error(int code, const char *msg) { return set_err(nullptr, code, msg); }
 } // namespace lbm
 
 extern "C" {

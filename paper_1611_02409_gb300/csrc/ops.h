@@ -33,6 +33,9 @@ Ops ops_d2q37(int storage);
 Ops ops_d3q103(int storage);
 void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);
 
+// Sets the handle-free error text (lbm_last_error(NULL)) and returns `code`.
+int set_global_error(int code, const char *msg);
+
 // FP64 lattice derivation (lattice_host.cu): fills c (Q x 3), w (Q) and r; returns Q or -1.
 int derive_lattice(int lattice, int (*c)[3], double *w, double *r);
 

@@ -105,6 +105,7 @@ def lib():
             L.lbm_get_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_kernel.argtypes = [vp, C.c_int]
+            L.lbm_field_totals_static.argtypes = [C.c_int, C.c_double, C.c_longlong, vp, vp, vp, vp, vp]
             L.lbm_autotune.argtypes = [vp, C.c_int, ip]
             _lib = L
     return _lib
@@ -219,6 +220,15 @@ def lbm_autotune(h, steps=10) -> int:
     chosen = C.c_int()
     _check(lib().lbm_autotune(h, int(steps), C.byref(chosen)), h)
     return chosen.value
+
+
+def lbm_field_totals_static(D, N_f, rho, u, T, out, stream=None):
+    """Conservation totals of device fields into the device array `out` (6 doubles),
+    without any allocation; see include/lbm.h."""
+    n = rho.numel()
+    s = C.c_void_p(stream) if isinstance(stream, int) else C.c_void_p(getattr(stream, "cuda_stream", 0) or 0)
+    return _check(lib().lbm_field_totals_static(int(D), float(N_f), n, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0],
+                                                _ptr(out)[0], s))
 
 
 def lbm_get_populations(h, g, hh):
