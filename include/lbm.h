@@ -181,6 +181,44 @@ int lbm_field_totals_static(int D, double N_f, long long n, const double *rho, c
 int lbm_get_populations(lbm_handle *h, double *g, double *hh, int mem);
 int lbm_set_populations(lbm_handle *h, const double *g, const double *hh, int mem);
 
+/* ---------------------------------------------------------------------------------
+ * Batched instances (no paper counterpart: a throughput layer).  Many independent 2-D
+ * D2Q37 FP32 instances (each with its own grid, boundaries, Pr, gamma, kappa, tau and
+ * walls) advance together: every time step is one persistent launch walking a device
+ * work list of 128-cell chunks over all active instances, followed by the wall, flip,
+ * residual and work-list kernels, all replayed from a CUDA graph.  An instance stops
+ * when its residual (as in lbm_diagnostics out[5]) falls below the tolerance at a
+ * check; the work list then drops it.  The batch owns its device memory and a stream.
+ * --------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* n >= 1 parameter sets (lattice LBM_D2Q37, storage LBM_FP32 for every one); every
+ * instance starts at the rest state.  Returns LBM_OK or an error (text in
+ * lbm_last_error(NULL)). */
+int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out);
+int lbm_batch_destroy(lbm_batch *b);
+
+/* Equilibrium initial state of instance i from its fields (layout and `mem` as in
+ * lbm_init_fields); marks it active and resets its step count and residual. */
+int lbm_batch_init_fields(lbm_batch *b, int i, const double *rho, const double *u, const double *T, int mem);
+
+/* Advances every active instance until all have converged (residual < tol at a check,
+ * checks every `check_every` steps) or `max_steps` steps have been taken by the batch.
+ * Synchronises.  *steps_taken (may be NULL) receives the number of batch steps run. */
+int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken);
+
+/* Per-instance status (host arrays of n entries, any may be NULL): steps taken, last
+ * residual (infinity before the second check), active flag (0 once converged). */
+int lbm_batch_status(lbm_batch *b, int *steps, double *residual, int *active);
+
+/* Fields of instance i (as lbm_moments). */
+int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u, double *T, double *Pi, double *q, int mem);
+
+/* Times the step kernel's tile sizes (128, 256 or 512 cells per work item) over
+ * `steps` steps on the current state and keeps the fastest; *chosen receives the tile.
+ * Resets every instance to the rest state (call before lbm_batch_init_fields). */
+int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen);
+
 #ifdef __cplusplus
 }
 #endif

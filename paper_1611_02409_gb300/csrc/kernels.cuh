@@ -229,15 +229,14 @@ struct WallParams {
     float thw[2];    // T_w - 1
 };
 
+// The wall procedure for one column x of wall b (0 bottom, 1 top) of buffer `buf`.
 template <int LAT, int ST>
-__global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const WallParams wp)
+__device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> &kp,
+                                            const WallParams &wp, int x, int b)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     static_assert(D == 2, "walls are 2-D");
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= kp.nx) return;
-    const int b = blockIdx.y;
     const int n = b == 0 ? 1 : -1;
     const int yw = b == 0 ? 0 : kp.ny - 1;
     const int small_x = kp.nx < 4;
@@ -295,6 +294,14 @@ __global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams
             Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, fmaf(rw, hk[k][i], hb) + t1[i]);
         }
     }
+}
+
+template <int LAT, int ST>
+__global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const WallParams wp)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    wall_column<LAT, ST>(buf, kp, wp, x, blockIdx.y);
 }
 
 // Macroscopic fields of the stored populations (FP64 out, any pointer may be null).

@@ -152,6 +152,52 @@ static int map_params(const lbm_params &p, Mapped &m)
     return LBM_OK;
 }
 
+} // extern "C"
+
+namespace lbm {
+// Validates p and fills c (host fields only: geometry, coefficients, lattice weights)
+// as lbm_create does; D and Q receive the lattice dimensions.  Returns an LBM status.
+int make_ctx(const lbm_params &pin, Ctx &c, int *D_out, int *Q_out, double *r_out)
+{
+    lbm_params p = pin;
+    Mapped mp;
+    int rc = map_params(p, mp);
+    if (rc) return rc;
+    if (mp.D == 2) p.nz = 1;
+    int cc[128][3];
+    double w[128], r;
+    const int Q = derive_lattice(p.lattice, cc, w, &r);
+    if (Q < 0) return set_err(nullptr, LBM_ERR_ARG, "lattice derivation failed");
+    memset(&c, 0, sizeof(c));
+    c.storage = p.storage;
+    c.walls = p.bc_y == LBM_WALLS;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.nz = p.nz;
+    c.gh = c.walls ? 2 : 0;
+    c.nys = p.ny + 2 * c.gh;
+    c.plane = (long long)p.nx * c.nys * p.nz;
+    c.omega = mp.omega;
+    c.kappa = p.kappa;
+    c.a_tr = (1.0 - p.kappa) * (1.0 - mp.nuG);
+    c.a_sig = (1.0 - p.kappa) * mp.nuG;
+    c.Nf = mp.Nf;
+    c.r = r;
+    for (int i = 0; i < Q; ++i) c.w[i] = w[i];
+    for (int b = 0; b < 2; ++b) {
+        for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
+        c.wall_T[b] = p.wall_T[b];
+    }
+    c.kernel = 1;
+    if (D_out) *D_out = mp.D;
+    if (Q_out) *Q_out = Q;
+    if (r_out) *r_out = r;
+    return mp.warn ? LBM_WARN_PR_RANGE : LBM_OK;
+}
+} // namespace lbm
+
+extern "C" {
+
 int lbm_map_params(const lbm_params *p, double *out)
 {
     if (!p || !out) return set_err(nullptr, LBM_ERR_ARG, "null argument");

@@ -33,6 +33,12 @@ Ops ops_d2q37(int storage);
 Ops ops_d3q103(int storage);
 void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);
 
+}  // namespace lbm
+struct lbm_params;
+namespace lbm {
+// Validation + mapping + lattice as lbm_create does it (lbm_api.cu).
+int make_ctx(const lbm_params &p, Ctx &c, int *D, int *Q, double *r);
+
 // Sets the handle-free error text (lbm_last_error(NULL)) and returns `code`.
 int set_global_error(int code, const char *msg);
 

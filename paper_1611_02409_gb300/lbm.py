@@ -105,6 +105,13 @@ def lib():
             L.lbm_get_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_kernel.argtypes = [vp, C.c_int]
+            L.lbm_batch_create.argtypes = [C.c_int, C.POINTER(lbm_params), C.POINTER(vp)]
+            L.lbm_batch_destroy.argtypes = [vp]
+            L.lbm_batch_init_fields.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+            L.lbm_batch_run.argtypes = [vp, C.c_int, C.c_double, C.c_int, ip]
+            L.lbm_batch_status.argtypes = [vp, ip, dp, ip]
+            L.lbm_batch_moments.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
+            L.lbm_batch_autotune.argtypes = [vp, C.c_int, ip]
             L.lbm_field_totals_static.argtypes = [C.c_int, C.c_double, C.c_longlong, vp, vp, vp, vp, vp]
             L.lbm_autotune.argtypes = [vp, C.c_int, ip]
             _lib = L
@@ -298,6 +305,93 @@ class Simulation:
         if getattr(self, "h", None):
             lbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------
+# Batched instances (lbm_batch_* in include/lbm.h)
+
+
+def lbm_batch_create(params_list):
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = C.c_void_p()
+    _check(lib().lbm_batch_create(len(params_list), arr, C.byref(b)))
+    return b
+
+
+def lbm_batch_destroy(b):
+    return _check(lib().lbm_batch_destroy(b))
+
+
+def lbm_batch_init_fields(b, i, rho, u, T):
+    mem = _mem_of(rho, u, T)
+    return _check(lib().lbm_batch_init_fields(b, int(i), _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0], mem))
+
+
+def lbm_batch_run(b, max_steps, tol, check_every=100) -> int:
+    done = C.c_int()
+    _check(lib().lbm_batch_run(b, int(max_steps), float(tol), int(check_every), C.byref(done)))
+    return done.value
+
+
+def lbm_batch_status(b, n):
+    steps = np.zeros(n, np.int32)
+    res = np.zeros(n)
+    act = np.zeros(n, np.int32)
+    _check(lib().lbm_batch_status(b, steps.ctypes.data_as(C.POINTER(C.c_int)), res.ctypes.data_as(C.POINTER(C.c_double)),
+                                  act.ctypes.data_as(C.POINTER(C.c_int))))
+    return steps, res, act
+
+
+def lbm_batch_moments(b, i, rho=None, u=None, T=None, Pi=None, q=None):
+    xs = [x for x in (rho, u, T, Pi, q) if x is not None]
+    mem = _mem_of(*xs) if xs else LBM_MEM_DEVICE
+    return _check(lib().lbm_batch_moments(b, int(i), *(_ptr(x)[0] for x in (rho, u, T, Pi, q)), mem))
+
+
+def lbm_batch_autotune(b, steps=20) -> int:
+    chosen = C.c_int()
+    _check(lib().lbm_batch_autotune(b, int(steps), C.byref(chosen)))
+    return chosen.value
+
+
+class Batch:
+    """Many independent 2-D D2Q37 FP32 instances stepped together."""
+
+    def __init__(self, param_dicts):
+        self.params = [make_params(**d) for d in param_dicts]
+        self.n = len(self.params)
+        self.b = lbm_batch_create(self.params)
+
+    def init(self, i, rho, u, T):
+        lbm_batch_init_fields(self.b, i, np.ascontiguousarray(rho, np.float64), np.ascontiguousarray(u, np.float64),
+                              np.ascontiguousarray(T, np.float64))
+
+    def run(self, max_steps, tol=0.0, check_every=100):
+        return lbm_batch_run(self.b, max_steps, tol, check_every)
+
+    def status(self):
+        return lbm_batch_status(self.b, self.n)
+
+    def moments(self, i):
+        p = self.params[i]
+        s = (p.ny, p.nx)
+        out = dict(rho=np.zeros(s), u=np.zeros((2,) + s), T=np.zeros(s), Pi=np.zeros((3,) + s), q=np.zeros((2,) + s))
+        lbm_batch_moments(self.b, i, out["rho"], out["u"], out["T"], out["Pi"], out["q"])
+        return out
+
+    def autotune(self, steps=20):
+        return lbm_batch_autotune(self.b, steps)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
