@@ -219,6 +219,31 @@ int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u, double *T, do
  * Resets every instance to the rest state (call before lbm_batch_init_fields). */
 int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen);
 
+/* ---------------------------------------------------------------------------------
+ * Surrogate network (no paper counterpart: the learned warm start).  A multilayer
+ * perceptron sizes[0] -> sizes[1] -> ... -> sizes[nlayers] with GELU on every hidden
+ * layer and a linear output, trained on the mean squared error with Adam.  Products run
+ * on the tensor cores in bfloat16 with FP32 accumulation; weights are kept in FP32.
+ * Parameters are packed per layer as W (sizes[l] x sizes[l+1], row-major) then b.
+ * All device work is queued on `stream`; calls that return host data synchronise.
+ * --------------------------------------------------------------------------------- */
+typedef struct lbm_mlp lbm_mlp;
+
+int lbm_mlp_create(int nlayers, const int *sizes, int max_batch, void *stream, lbm_mlp **out);
+int lbm_mlp_destroy(lbm_mlp *h);
+long long lbm_mlp_num_params(const lbm_mlp *h);
+/* Host FP32 parameters in (resets the Adam state) / out; grads (may be NULL) receives the
+ * gradients of the last lbm_mlp_backward in the same packing. */
+int lbm_mlp_set_params(lbm_mlp *h, const float *params);
+int lbm_mlp_get_params(lbm_mlp *h, float *params, float *grads);
+/* x: device [batch][sizes[0]] FP32; y (device, may be NULL): [batch][sizes[nlayers]]. */
+int lbm_mlp_forward(lbm_mlp *h, int batch, const float *x, float *y);
+/* Gradients of mean((y - target)^2) for the last forward; target: device FP32 like y;
+ * *loss (may be NULL, synchronises) receives the loss. */
+int lbm_mlp_backward(lbm_mlp *h, const float *target, double *loss);
+/* One Adam step (Kingma & Ba, bias-corrected) with the last gradients. */
+int lbm_mlp_adam(lbm_mlp *h, float lr, float b1, float b2, float eps);
+
 #ifdef __cplusplus
 }
 #endif

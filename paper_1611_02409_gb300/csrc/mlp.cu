@@ -1,0 +1,379 @@
+// Surrogate network kernels (include/lbm.h, lbm_mlp_*): a multilayer perceptron with
+// GELU hidden layers and a linear output, trained with the mean squared error and Adam.
+// Matrix products run on the tensor cores in bfloat16 with FP32 accumulation
+// (mma.sync m16n8k16); master weights, Adam moments, pre-activations and gradients are
+// FP32.  The operands held in bfloat16 are: the network input, the weights, every hidden
+// activation fed to the next layer, and the backward deltas fed to the two gradient
+// products.  The GEMMs here are small (batch <= a few hundred, width <= 1024).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "ops.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[N]); op(A)[m][k] = ta ? A[k lda + m] :
+// A[m lda + k], op(B)[k][n] = tb ? B[n ldb + k] : B[k ldb + n].  Epilogue: Cpre (FP32,
+// pre-activation) if given, C = act(...) (act 1 = GELU), and its bfloat16 copy Cbf if given.
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int lda, int ta,
+                                              const bf16 *__restrict__ B, int ldb, int tb, float *C, int ldc,
+                                              const float *__restrict__ bias, int act, float *Cpre, bf16 *Cbf)
+{
+    __shared__ bf16 As[BM][BK + 8];
+    __shared__ bf16 Bs[BN][BK + 8];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int wm = w >> 1, wn = w & 1;
+    const int g = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    const bf16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 128) {
+            const int m = e / BK, k = e % BK, gm = m0 + m, gk = k0 + k;
+            As[m][k] = (gm < M && gk < K) ? (ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
+        }
+        for (int e = tid; e < BN * BK; e += 128) {
+            const int n = e / BK, k = e % BK, gn = n0 + n, gk = k0 + k;
+            Bs[n][k] = (gn < N && gk < K) ? (tb ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn]) : zero;
+        }
+        __syncthreads();
+        uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const int r = wm * 32 + mi * 16 + g;
+            af[mi][0] = pack_bf16(As[r][2 * tq], As[r][2 * tq + 1]);
+            af[mi][1] = pack_bf16(As[r + 8][2 * tq], As[r + 8][2 * tq + 1]);
+            af[mi][2] = pack_bf16(As[r][2 * tq + 8], As[r][2 * tq + 9]);
+            af[mi][3] = pack_bf16(As[r + 8][2 * tq + 8], As[r + 8][2 * tq + 9]);
+        }
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const int c = wn * 32 + ni * 8 + g;
+            bfr[ni][0] = pack_bf16(Bs[c][2 * tq], Bs[c][2 * tq + 1]);
+            bfr[ni][1] = pack_bf16(Bs[c][2 * tq + 8], Bs[c][2 * tq + 9]);
+        }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                float *d = acc[mi][ni];
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                             "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                             : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bfr[ni][0]),
+                               "r"(bfr[ni][1]));
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r = m0 + wm * 32 + mi * 16 + g + (k >= 2 ? 8 : 0);
+                const int c = n0 + wn * 32 + ni * 8 + 2 * tq + (k & 1);
+                if (r < M && c < N) {
+                    float v = acc[mi][ni][k] + (bias ? bias[c] : 0.f);
+                    const long long o = (long long)r * ldc + c;
+                    if (Cpre) Cpre[o] = v;
+                    if (act == 1) v = gelu_f(v);
+                    if (C) C[o] = v;
+                    if (Cbf) Cbf[o] = __float2bfloat16_rn(v);
+                }
+            }
+}
+
+__global__ void k_f2bf(const float *__restrict__ s, bf16 *d, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = __float2bfloat16_rn(s[i]);
+}
+
+// dz = 2 (y - t) / n, its bfloat16 copy, and per-block partial sums of (y - t)^2.
+__global__ void __launch_bounds__(256) k_mse(const float *__restrict__ y, const float *__restrict__ t, float *dz,
+                                             bf16 *dzb, long long n, double *partials)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float d = y[i] - t[i];
+        acc += (double)d * d;
+        const float gz = 2.f * d / (float)n;
+        dz[i] = gz;
+        dzb[i] = __float2bfloat16_rn(gz);
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double *p, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += p[i];
+        *out = s;
+    }
+}
+
+// dz = da * GELU'(z) and its bfloat16 copy.
+__global__ void k_gelu_bwd(const float *__restrict__ da, const float *__restrict__ z, float *dz, bf16 *dzb,
+                           long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = da[i] * gelu_grad_f(z[i]);
+        dz[i] = v;
+        dzb[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// db[c] = sum_r dz[r][c] (fixed order per column).
+__global__ void k_colsum(const float *__restrict__ dz, int rows, int cols, float *db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += dz[(long long)r * cols + c];
+    db[c] = s;
+}
+
+__global__ void k_adam(float *w, const float *__restrict__ g, float *m, float *v, long long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+} // namespace
+
+struct lbm_mlp {
+    int L = 0, maxb = 0;
+    std::vector<int> sizes;
+    std::vector<long long> woff, boff;  // offsets into the packed parameter vector
+    long long nparam = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // packed FP32
+    bf16 *wb = nullptr;                                            // bfloat16 weights (packed like p)
+    bf16 *xb = nullptr;                                            // input [maxb][sizes[0]]
+    std::vector<float *> z;                                        // pre-activations per layer
+    std::vector<bf16 *> ab;                                        // hidden activations (bf16)
+    float *dz = nullptr, *da = nullptr;
+    bf16 *dzb = nullptr;
+    double *partials = nullptr, *dloss = nullptr;
+    int batch = 0;
+    long long t = 0;
+    cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+int mfail(const char *msg) { return lbm::set_global_error(LBM_ERR_ARG, msg); }
+
+#define LBM_MCK(call)                                                                                          \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess) return lbm::set_global_error(LBM_ERR_CUDA, cudaGetErrorString(e_));             \
+    } while (0)
+
+void gemm(lbm_mlp *h, int M, int N, int K, const bf16 *A, int lda, int ta, const bf16 *B, int ldb, int tb, float *C,
+          int ldc, const float *bias, int act, float *Cpre, bf16 *Cbf)
+{
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    k_gemm<<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf);
+}
+
+int grid1(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+} // namespace
+
+extern "C" {
+
+int lbm_mlp_create(int nlayers, const int *sizes, int max_batch, void *stream, lbm_mlp **out)
+{
+    if (!out || !sizes || nlayers < 1 || max_batch < 1) return mfail("need nlayers >= 1, sizes, max_batch >= 1");
+    for (int i = 0; i <= nlayers; ++i)
+        if (sizes[i] < 1) return mfail("layer sizes must be >= 1");
+    lbm_mlp *h = new lbm_mlp();
+    h->L = nlayers;
+    h->maxb = max_batch;
+    h->sizes.assign(sizes, sizes + nlayers + 1);
+    h->stream = (cudaStream_t)stream;
+    int maxn = 0;
+    for (int l = 0; l < nlayers; ++l) {
+        h->woff.push_back(h->nparam);
+        h->nparam += (long long)sizes[l] * sizes[l + 1];
+        h->boff.push_back(h->nparam);
+        h->nparam += sizes[l + 1];
+        maxn = std::max(maxn, std::max(sizes[l], sizes[l + 1]));
+    }
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+    };
+    al((void **)&h->p, sizeof(float) * h->nparam);
+    al((void **)&h->g, sizeof(float) * h->nparam);
+    al((void **)&h->m, sizeof(float) * h->nparam);
+    al((void **)&h->v, sizeof(float) * h->nparam);
+    al((void **)&h->wb, sizeof(bf16) * h->nparam);
+    al((void **)&h->xb, sizeof(bf16) * (size_t)max_batch * sizes[0]);
+    h->z.resize(nlayers);
+    h->ab.resize(nlayers);
+    for (int l = 0; l < nlayers; ++l) {
+        al((void **)&h->z[l], sizeof(float) * (size_t)max_batch * sizes[l + 1]);
+        al((void **)&h->ab[l], sizeof(bf16) * (size_t)max_batch * sizes[l + 1]);
+    }
+    al((void **)&h->dz, sizeof(float) * (size_t)max_batch * maxn);
+    al((void **)&h->da, sizeof(float) * (size_t)max_batch * maxn);
+    al((void **)&h->dzb, sizeof(bf16) * (size_t)max_batch * maxn);
+    al((void **)&h->partials, sizeof(double) * 4096);
+    al((void **)&h->dloss, sizeof(double));
+    if (e != cudaSuccess) {
+        lbm_mlp_destroy(h);
+        return lbm::set_global_error(LBM_ERR_NOMEM, cudaGetErrorString(e));
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_mlp_destroy(lbm_mlp *h)
+{
+    if (!h) return LBM_OK;
+    cudaStreamSynchronize(h->stream);
+    for (void *p : {(void *)h->p, (void *)h->g, (void *)h->m, (void *)h->v, (void *)h->wb, (void *)h->xb,
+                    (void *)h->dz, (void *)h->da, (void *)h->dzb, (void *)h->partials, (void *)h->dloss})
+        if (p) cudaFree(p);
+    for (auto *p : h->z)
+        if (p) cudaFree(p);
+    for (auto *p : h->ab)
+        if (p) cudaFree(p);
+    delete h;
+    return LBM_OK;
+}
+
+long long lbm_mlp_num_params(const lbm_mlp *h) { return h ? h->nparam : -1; }
+
+int lbm_mlp_set_params(lbm_mlp *h, const float *params)
+{
+    if (!h || !params) return mfail("null argument");
+    LBM_MCK(cudaMemcpyAsync(h->p, params, sizeof(float) * h->nparam, cudaMemcpyHostToDevice, h->stream));
+    LBM_MCK(cudaMemsetAsync(h->m, 0, sizeof(float) * h->nparam, h->stream));
+    LBM_MCK(cudaMemsetAsync(h->v, 0, sizeof(float) * h->nparam, h->stream));
+    k_f2bf<<<grid1(h->nparam), 256, 0, h->stream>>>(h->p, h->wb, h->nparam);
+    h->t = 0;
+    LBM_MCK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_mlp_get_params(lbm_mlp *h, float *params, float *grads)
+{
+    if (!h) return mfail("null handle");
+    if (params) LBM_MCK(cudaMemcpyAsync(params, h->p, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
+    if (grads) LBM_MCK(cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
+    LBM_MCK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_mlp_forward(lbm_mlp *h, int batch, const float *x, float *y)
+{
+    if (!h || !x || batch < 1 || batch > h->maxb) return mfail("bad forward arguments");
+    h->batch = batch;
+    const int *S = h->sizes.data();
+    k_f2bf<<<grid1((long long)batch * S[0]), 256, 0, h->stream>>>(x, h->xb, (long long)batch * S[0]);
+    const bf16 *in = h->xb;
+    for (int l = 0; l < h->L; ++l) {
+        const bool last = l == h->L - 1;
+        gemm(h, batch, S[l + 1], S[l], in, S[l], 0, h->wb + h->woff[l], S[l + 1], 0, last ? h->z[l] : nullptr,
+             S[l + 1], h->p + h->boff[l], last ? 0 : 1, last ? nullptr : h->z[l], last ? nullptr : h->ab[l]);
+        in = h->ab[l];
+    }
+    if (y)
+        LBM_MCK(cudaMemcpyAsync(y, h->z[h->L - 1], sizeof(float) * (size_t)batch * S[h->L], cudaMemcpyDeviceToDevice,
+                                h->stream));
+    LBM_MCK(cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_mlp_backward(lbm_mlp *h, const float *target, double *loss)
+{
+    if (!h || !target || h->batch < 1) return mfail("bad backward arguments (run lbm_mlp_forward first)");
+    const int B = h->batch;
+    const int *S = h->sizes.data();
+    const long long nout = (long long)B * S[h->L];
+    const int nb = grid1(nout);
+    k_mse<<<nb, 256, 0, h->stream>>>(h->z[h->L - 1], target, h->dz, h->dzb, nout, h->partials);
+    k_sum_partials<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dloss);
+    for (int l = h->L - 1; l >= 0; --l) {
+        const int K = S[l], N = S[l + 1];
+        const bf16 *act = l == 0 ? h->xb : h->ab[l - 1];
+        // dW = act^T dz   (K x N)
+        gemm(h, K, N, B, act, K, 1, h->dzb, N, 0, h->g + h->woff[l], N, nullptr, 0, nullptr, nullptr);
+        k_colsum<<<(N + 127) / 128, 128, 0, h->stream>>>(h->dz, B, N, h->g + h->boff[l]);
+        if (l > 0) {
+            // da = dz W^T   (B x K), then dz = da GELU'(z_{l-1})
+            gemm(h, B, K, N, h->dzb, N, 0, h->wb + h->woff[l], N, 1, h->da, K, nullptr, 0, nullptr, nullptr);
+            k_gelu_bwd<<<grid1((long long)B * K), 256, 0, h->stream>>>(h->da, h->z[l - 1], h->dz, h->dzb,
+                                                                       (long long)B * K);
+        }
+    }
+    LBM_MCK(cudaGetLastError());
+    if (loss) {
+        double v = 0.0;
+        LBM_MCK(cudaMemcpyAsync(&v, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        LBM_MCK(cudaStreamSynchronize(h->stream));
+        *loss = v / (double)nout;
+    }
+    return LBM_OK;
+}
+
+int lbm_mlp_adam(lbm_mlp *h, float lr, float b1, float b2, float eps)
+{
+    if (!h) return mfail("null handle");
+    h->t += 1;
+    const float c1 = 1.f - powf(b1, (float)h->t), c2 = 1.f - powf(b2, (float)h->t);
+    k_adam<<<grid1(h->nparam), 256, 0, h->stream>>>(h->p, h->g, h->m, h->v, h->nparam, lr, b1, b2, eps, c1, c2);
+    k_f2bf<<<grid1(h->nparam), 256, 0, h->stream>>>(h->p, h->wb, h->nparam);
+    LBM_MCK(cudaGetLastError());
+    return LBM_OK;
+}
+
+} // extern "C"

@@ -79,7 +79,7 @@ _lib = None
 def exported_names() -> list[str]:
     """Entry points declared in include/lbm.h."""
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*|void)\s*\*?\s*(lbm_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char \*|void)\s*\*?\s*(lbm_\w+)\s*\(", src, re.M)))
 
 
 def lib():
@@ -112,6 +112,15 @@ def lib():
             L.lbm_batch_status.argtypes = [vp, ip, dp, ip]
             L.lbm_batch_moments.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
             L.lbm_batch_autotune.argtypes = [vp, C.c_int, ip]
+            L.lbm_mlp_create.argtypes = [C.c_int, ip, C.c_int, vp, C.POINTER(vp)]
+            L.lbm_mlp_destroy.argtypes = [vp]
+            L.lbm_mlp_num_params.argtypes = [vp]
+            L.lbm_mlp_num_params.restype = C.c_longlong
+            L.lbm_mlp_set_params.argtypes = [vp, vp]
+            L.lbm_mlp_get_params.argtypes = [vp, vp, vp]
+            L.lbm_mlp_forward.argtypes = [vp, C.c_int, vp, vp]
+            L.lbm_mlp_backward.argtypes = [vp, vp, dp]
+            L.lbm_mlp_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
             L.lbm_field_totals_static.argtypes = [C.c_int, C.c_double, C.c_longlong, vp, vp, vp, vp, vp]
             L.lbm_autotune.argtypes = [vp, C.c_int, ip]
             _lib = L
@@ -392,6 +401,81 @@ class Batch:
         if getattr(self, "b", None):
             lbm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------
+# Surrogate network (lbm_mlp_* in include/lbm.h)
+
+
+class MLP:
+    """GELU multilayer perceptron on the tensor cores (bfloat16 products, FP32 master
+    weights); parameters exchanged as [[W (k x n), b (n)], ...] float arrays."""
+
+    def __init__(self, sizes, max_batch, stream=None):
+        import torch
+        self.torch = torch
+        self.sizes = list(sizes)
+        arr = (C.c_int * len(sizes))(*sizes)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = C.c_void_p()
+        _check(lib().lbm_mlp_create(len(sizes) - 1, arr, int(max_batch), C.c_void_p(self.stream.cuda_stream),
+                                    C.byref(self.h)))
+        self.n = lib().lbm_mlp_num_params(self.h)
+
+    def _pack(self, params):
+        return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in params]).astype(np.float32)
+
+    def _unpack(self, flat):
+        out, o = [], 0
+        for k, n in zip(self.sizes[:-1], self.sizes[1:]):
+            W = flat[o:o + k * n].reshape(k, n)
+            o += k * n
+            b = flat[o:o + n]
+            o += n
+            out.append([W.astype(np.float64), b.astype(np.float64)])
+        return out
+
+    def set_params(self, params):
+        flat = np.ascontiguousarray(self._pack(params))
+        assert flat.size == self.n
+        _check(lib().lbm_mlp_set_params(self.h, C.c_void_p(flat.ctypes.data)))
+
+    def get_params(self, with_grads=False):
+        p = np.zeros(self.n, np.float32)
+        g = np.zeros(self.n, np.float32) if with_grads else None
+        _check(lib().lbm_mlp_get_params(self.h, C.c_void_p(p.ctypes.data),
+                                        C.c_void_p(g.ctypes.data) if g is not None else None))
+        return (self._unpack(p), self._unpack(g)) if with_grads else self._unpack(p)
+
+    def forward(self, x):
+        """x: torch CUDA float32 [batch, sizes[0]] -> y [batch, sizes[-1]] (torch)."""
+        t = self.torch
+        x = x.to(device="cuda", dtype=t.float32).contiguous()
+        y = t.empty((x.shape[0], self.sizes[-1]), dtype=t.float32, device="cuda")
+        _check(lib().lbm_mlp_forward(self.h, int(x.shape[0]), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def backward(self, target, want_loss=True):
+        t = self.torch
+        target = target.to(device="cuda", dtype=t.float32).contiguous()
+        loss = C.c_double()
+        _check(lib().lbm_mlp_backward(self.h, C.c_void_p(target.data_ptr()), C.byref(loss) if want_loss else None))
+        self._keep = target
+        return loss.value if want_loss else None
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        _check(lib().lbm_mlp_adam(self.h, lr, b1, b2, eps))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_mlp_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
