@@ -128,6 +128,15 @@ int lbm_map_params(const lbm_params *p, double *out);
  * on the handle's stream).  Resets the step counter. */
 int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const double *T, int mem);
 
+/* lbm_init_fields plus a non-equilibrium part (warm start from predicted profiles;
+ * no paper counterpart): Pi[D(D+1)/2][n] (rho sigma as lbm_moments reports it, may be
+ * NULL) contributes its traceless part of Pi - rho T delta through the second Hermite
+ * term of g (reproducing Pi; mass, momentum and energy unchanged); q[D][n] (may be NULL)
+ * a heat flux, (D+2)/(D+2+N_f) of it through the third Hermite term of g and the rest
+ * through the first of h. */
+int lbm_init_fields_neq(lbm_handle *h, const double *rho, const double *u, const double *T, const double *Pi,
+                        const double *q, int mem);
+
 /* Queues nsteps fused pull-stream + collide steps (+ the wall kernel when bc_y is
  * LBM_WALLS) on the handle's stream.  nsteps >= 0. */
 int lbm_step(lbm_handle *h, int nsteps);
@@ -201,6 +210,9 @@ int lbm_batch_destroy(lbm_batch *b);
 /* Equilibrium initial state of instance i from its fields (layout and `mem` as in
  * lbm_init_fields); marks it active and resets its step count and residual. */
 int lbm_batch_init_fields(lbm_batch *b, int i, const double *rho, const double *u, const double *T, int mem);
+/* ... with the non-equilibrium part of lbm_init_fields_neq. */
+int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const double *u, const double *T,
+                              const double *Pi, const double *q, int mem);
 
 /* Advances every active instance until all have converged (residual < tol at a check,
  * checks every `check_every` steps) or `max_steps` steps have been taken by the batch.

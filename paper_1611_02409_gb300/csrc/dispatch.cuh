@@ -55,7 +55,13 @@ template <int LAT, int ST> struct Launch {
 
     static void init(const Ctx &c, void *dst, const double *rho, const double *u, const double *T_, cudaStream_t st)
     {
-        k_init<LAT, ST><<<rows_grid(c, c.nys, 64), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_);
+        k_init<LAT, ST><<<rows_grid(c, c.nys, 64), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_, nullptr,
+                                                               nullptr);
+    }
+    static void init_neq(const Ctx &c, void *dst, const double *rho, const double *u, const double *T_,
+                         const double *Pi, const double *q, cudaStream_t st)
+    {
+        k_init<LAT, ST><<<rows_grid(c, c.nys, 64), 64, 0, st>>>((T *)dst, make_kparams<LAT>(c), rho, u, T_, Pi, q);
     }
     // shared-memory-staged path: 2-D, nx a multiple of the tile width
     static bool staged_ok(const Ctx &c)
@@ -133,6 +139,7 @@ template <int LAT, int ST> Ops make_ops_st()
 {
     Ops o;
     o.init = &Launch<LAT, ST>::init;
+    o.init_neq = &Launch<LAT, ST>::init_neq;
     o.step = &Launch<LAT, ST>::step;
     o.walls = &Launch<LAT, ST>::walls;
     o.moments = &Launch<LAT, ST>::moments;

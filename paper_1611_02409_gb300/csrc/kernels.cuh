@@ -178,10 +178,16 @@ __device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho,
 
 // Initial populations (equilibrium of the fields, Lambda = T delta) for every stored
 // cell; ghost rows take the nearest domain row's field.  Fields are FP64 device arrays.
+// Optional non-equilibrium parts (warm start): Pi (D(D+1)/2 x n, rho sigma as
+// lbm_moments reports it) adds the traceless part P of Pi - rho T delta to g through the
+// second Hermite term, s_i += P : (xi xi - delta) / 2, which reproduces Pi and leaves
+// mass, momentum and energy unchanged; q (D x n) adds a heat flux split by heat capacity:
+// the translational share (D+2)/(D+2+N_f) to g through the third Hermite term
+// s_i += (xi^2 - D - 2)(q_g . xi)/(D + 2), the internal share to h, t_i += q_h . xi.
 template <int LAT, int ST>
 __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<LAT> kp,
                        const double *__restrict__ rho, const double *__restrict__ u,
-                       const double *__restrict__ T)
+                       const double *__restrict__ T, const double *__restrict__ Pi, const double *__restrict__ q)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
@@ -197,6 +203,41 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<
     for (int a = 0; a < D; ++a) vv[a] = (float)(u[a * n + f] / (double)kp.r_d);
     float s[Q], t[Q];
     maxwell_pops<LAT>(kp, (float)(rho[f] - 1.0), vv, (float)(T[f] - 1.0), s, t);
+    if (Pi || q) {
+        float P[D][D], qg[D], qh[D];
+        const double rT = rho[f] * T[f];
+        int k = 0;
+        for (int a = 0; a < D; ++a)
+            for (int b = a; b < D; ++b) {
+                const double v = Pi ? Pi[(k++) * n + f] - (a == b ? rT : 0.0) : 0.0;
+                P[a][b] = P[b][a] = (float)v;
+            }
+        float tr = 0.f;
+        for (int a = 0; a < D; ++a) tr += P[a][a];
+        for (int a = 0; a < D; ++a) P[a][a] -= tr / D;
+        const double share = (D + 2.0) / (D + 2.0 + kp.Nf);
+        for (int a = 0; a < D; ++a) {
+            const double qa = q ? q[a * n + f] : 0.0;
+            qg[a] = (float)(qa * share);
+            qh[a] = (float)(qa * (1.0 - share));
+        }
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            float xi[D], x2 = 0.f, qgx = 0.f, qhx = 0.f, pxx = 0.f;
+            static_for<0, D>([&](auto AA) {
+                constexpr int a = decltype(AA)::value;
+                xi[a] = kp.r * (float)cv<LAT, I, a>();
+            });
+            for (int a = 0; a < D; ++a) {
+                x2 += xi[a] * xi[a];
+                qgx += qg[a] * xi[a];
+                qhx += qh[a] * xi[a];
+                for (int b = 0; b < D; ++b) pxx += P[a][b] * xi[a] * xi[b];
+            }
+            s[I] += 0.5f * pxx + (x2 - (float)(D + 2)) * qgx / (float)(D + 2);
+            t[I] += qhx;
+        });
+    }
     const long long o = cell_index<LAT>(kp, x, ys, z);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

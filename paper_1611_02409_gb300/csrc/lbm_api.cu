@@ -383,6 +383,43 @@ int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const dou
     return LBM_OK;
 }
 
+int lbm_init_fields_neq(lbm_handle *h, const double *rho, const double *u, const double *T, const double *Pi,
+                        const double *q, int mem)
+{
+    if (!h || !rho || !u || !T) return set_err(h, LBM_ERR_ARG, "null field");
+    const long long n = ncell(h);
+    const int D = h->D, np = D * (D + 1) / 2;
+    const double *dr = rho, *du = u, *dT = T, *dP = Pi, *dq = q;
+    if (mem == LBM_MEM_HOST) {
+        int rc = ensure_stage(h, sizeof(double) * n * (2 + D + np + D));
+        if (rc) return rc;
+        double *s = h->d_stage;
+        LBM_CK(h, cudaMemcpyAsync(s, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        LBM_CK(h, cudaMemcpyAsync(s + n, u, sizeof(double) * n * D, cudaMemcpyHostToDevice, h->stream));
+        LBM_CK(h, cudaMemcpyAsync(s + n * (1 + D), T, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        dr = s;
+        du = s + n;
+        dT = s + n * (1 + D);
+        dP = dq = nullptr;
+        if (Pi) {
+            LBM_CK(h, cudaMemcpyAsync(s + n * (2 + D), Pi, sizeof(double) * n * np, cudaMemcpyHostToDevice, h->stream));
+            dP = s + n * (2 + D);
+        }
+        if (q) {
+            LBM_CK(h, cudaMemcpyAsync(s + n * (2 + D + np), q, sizeof(double) * n * D, cudaMemcpyHostToDevice,
+                                      h->stream));
+            dq = s + n * (2 + D + np);
+        }
+    } else if (mem != LBM_MEM_DEVICE) {
+        return set_err(h, LBM_ERR_ARG, "bad mem");
+    }
+    h->ops.init_neq(h->ctx, h->buf[h->cur], dr, du, dT, dP, dq, h->stream);
+    LBM_CK(h, cudaGetLastError());
+    h->steps = 0;
+    h->have_snap = 0;
+    return LBM_OK;
+}
+
 int lbm_step(lbm_handle *h, int nsteps)
 {
     if (!h || nsteps < 0) return set_err(h, LBM_ERR_ARG, "bad nsteps");

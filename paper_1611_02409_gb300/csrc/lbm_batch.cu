@@ -382,24 +382,39 @@ int lbm_batch_destroy(lbm_batch *b)
 
 int lbm_batch_init_fields(lbm_batch *b, int i, const double *rho, const double *u, const double *T, int mem)
 {
+    return lbm_batch_init_fields_neq(b, i, rho, u, T, nullptr, nullptr, mem);
+}
+
+int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const double *u, const double *T,
+                              const double *Pi, const double *q, int mem)
+{
     if (!b || i < 0 || i >= b->n || !rho || !u || !T) return bfail(b, LBM_ERR_ARG, "bad instance or null field");
     const Ctx &c = b->ctx[i];
     const size_t n = (size_t)c.nx * c.ny;
     Inst in;
     LBM_BCK(b, cudaMemcpyAsync(&in, b->d_inst + i, sizeof(Inst), cudaMemcpyDeviceToHost, b->stream));
     LBM_BCK(b, cudaStreamSynchronize(b->stream));
-    const double *dr = rho, *du = u, *dT = T;
+    const double *dr = rho, *du = u, *dT = T, *dP = Pi, *dq = q;
     double *stage = nullptr;
     if (mem == LBM_MEM_HOST) {
-        LBM_BCK(b, cudaMalloc(&stage, sizeof(double) * n * 4));
+        LBM_BCK(b, cudaMalloc(&stage, sizeof(double) * n * 9));
         LBM_BCK(b, cudaMemcpyAsync(stage, rho, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream));
         LBM_BCK(b, cudaMemcpyAsync(stage + n, u, sizeof(double) * n * 2, cudaMemcpyHostToDevice, b->stream));
         LBM_BCK(b, cudaMemcpyAsync(stage + 3 * n, T, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream));
         dr = stage;
         du = stage + n;
         dT = stage + 3 * n;
+        dP = dq = nullptr;
+        if (Pi) {
+            LBM_BCK(b, cudaMemcpyAsync(stage + 4 * n, Pi, sizeof(double) * n * 3, cudaMemcpyHostToDevice, b->stream));
+            dP = stage + 4 * n;
+        }
+        if (q) {
+            LBM_BCK(b, cudaMemcpyAsync(stage + 7 * n, q, sizeof(double) * n * 2, cudaMemcpyHostToDevice, b->stream));
+            dq = stage + 7 * n;
+        }
     }
-    Launch<LAT, ST>::init(c, b->d_arena + in.buf[in.cur], dr, du, dT, b->stream);
+    Launch<LAT, ST>::init_neq(c, b->d_arena + in.buf[in.cur], dr, du, dT, dP, dq, b->stream);
     in.active = 1;
     in.steps = 0;
     in.have_snap = 0;

@@ -18,6 +18,8 @@ struct Ctx {
 
 struct Ops {
     void (*init)(const Ctx &, void *dst, const double *rho, const double *u, const double *T, cudaStream_t);
+    void (*init_neq)(const Ctx &, void *dst, const double *rho, const double *u, const double *T, const double *Pi,
+                     const double *q, cudaStream_t);
     void (*step)(const Ctx &, const void *src, void *dst, cudaStream_t);
     void (*walls)(const Ctx &, void *buf, cudaStream_t);
     void (*moments)(const Ctx &, const void *buf, double *rho, double *u, double *T, double *Pi, double *q,

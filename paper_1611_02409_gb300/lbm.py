@@ -99,6 +99,8 @@ def lib():
             L.lbm_map_params.argtypes = [C.POINTER(lbm_params), dp]
             L.lbm_coefficients.argtypes = [vp, dp]
             L.lbm_init_fields.argtypes = [vp, vp, vp, vp, C.c_int]
+            L.lbm_init_fields_neq.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
+            L.lbm_batch_init_fields_neq.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
             L.lbm_step.argtypes = [vp, C.c_int]
             L.lbm_moments.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
             L.lbm_diagnostics.argtypes = [vp, dp]
@@ -192,6 +194,11 @@ def lbm_destroy(h):
 def lbm_init_fields(h, rho, u, T):
     mem = _mem_of(rho, u, T)
     return _check(lib().lbm_init_fields(h, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0], mem), h)
+
+
+def lbm_init_fields_neq(h, rho, u, T, Pi=None, q=None):
+    mem = _mem_of(*[x for x in (rho, u, T, Pi, q) if x is not None])
+    return _check(lib().lbm_init_fields_neq(h, *(_ptr(x)[0] for x in (rho, u, T, Pi, q)), mem), h)
 
 
 def lbm_step(h, nsteps=1):
@@ -380,6 +387,11 @@ class Batch:
     def init(self, i, rho, u, T):
         lbm_batch_init_fields(self.b, i, np.ascontiguousarray(rho, np.float64), np.ascontiguousarray(u, np.float64),
                               np.ascontiguousarray(T, np.float64))
+
+    def init_neq(self, i, rho, u, T, Pi=None, q=None):
+        f = lambda a: None if a is None else np.ascontiguousarray(a, np.float64)
+        xs = [f(a) for a in (rho, u, T, Pi, q)]
+        _check(lib().lbm_batch_init_fields_neq(self.b, int(i), *(_ptr(x)[0] for x in xs), LBM_MEM_HOST))
 
     def run(self, max_steps, tol=0.0, check_every=100):
         return lbm_batch_run(self.b, max_steps, tol, check_every)

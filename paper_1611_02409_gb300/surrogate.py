@@ -1,0 +1,200 @@
+"""Learned warm start of thermal Couette channels.
+
+A multilayer perceptron (5 -> 4 x 512 -> 4 x 256, GELU, bfloat16 products with FP32
+accumulation, trained on the GPU by the library's own kernels, lbm_mlp_*) maps the
+channel parameters (Pr, gamma, wall Mach number, tau, wall temperature difference) to
+the steady profiles of u_x, T, Pi_xy and q_y at 256 points of y/H.  Pi_xy and q_y are
+learned times (ny - 1), since in steady Couette flow they scale as 1/H.  The training
+profiles are steady channels the scheme itself computes (one batch, run to residual
+`tol`).  A prediction initialises a channel with its equilibrium plus the predicted
+non-equilibrium stress and heat flux (lbm_batch_init_fields_neq).  The plain scheme
+from rest remains the reference for the converged state.
+
+    python -m paper_1611_02409_gb300.surrogate --out study.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import sweep
+
+NPTS = 256
+SIZES = [5, 512, 512, 512, 512, 4 * NPTS]
+X_LO = np.array([0.5, 1.1, 0.01, 0.6, -0.05])
+X_HI = np.array([2.0, 1.67, 0.1, 1.0, 0.05])
+
+
+def draw_channels(n, seed, H=None, H_range=(64, 512)):
+    """n channel cases with the sweep's parameter distribution; fixed height H if given."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        x = rng.uniform(X_LO, X_HI)
+        h = H if H is not None else int(rng.integers(H_range[0], H_range[1] + 1))
+        out.append(sweep.channel_case(*x, h))
+    return out
+
+
+def glorot(sizes, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for k, n in zip(sizes[:-1], sizes[1:]):
+        a = np.sqrt(6.0 / (k + n))
+        params.append([rng.uniform(-a, a, size=(k, n)), np.zeros(n)])
+    return params
+
+
+class Surrogate:
+    """The profile network plus its input/output normalisation."""
+
+    def __init__(self, lbm, seed=0, max_batch=512, sizes=SIZES):
+        import torch
+        self.torch = torch
+        self.sizes = list(sizes)
+        self.net = lbm.MLP(self.sizes, max_batch=max_batch)
+        self.net.set_params(glorot(self.sizes, seed))
+        self.y_mean = None
+        self.y_std = None
+
+    def _x(self, X):
+        return self.torch.tensor(2.0 * (X - X_LO) / (X_HI - X_LO) - 1.0, dtype=self.torch.float32, device="cuda")
+
+    def fit(self, X, Y, iters=3000, lr=1e-3, log_every=500):
+        """X [n, 5] channel inputs, Y [n, 4, NPTS] profiles; full-batch Adam."""
+        t = self.torch
+        Yf = Y.reshape(len(Y), -1)
+        self.y_mean = Yf.mean(0)
+        self.y_std = np.maximum(Yf.std(0), 1e-6 * max(Yf.std(0).max(), 1e-30))
+        xt = self._x(X)
+        yt = t.tensor((Yf - self.y_mean) / self.y_std, dtype=t.float32, device="cuda")
+        losses = []
+        for it in range(iters):
+            self.net.forward(xt)
+            want = it % log_every == 0 or it == iters - 1
+            loss = self.net.backward(yt, want_loss=want)
+            if want:
+                losses.append((it, loss))
+            step_lr = lr if it < 0.7 * iters else lr * 0.2
+            self.net.adam(lr=step_lr)
+        return losses
+
+    def predict(self, X):
+        y = self.net.forward(self._x(X)).cpu().numpy().astype(np.float64)
+        return (y * self.y_std + self.y_mean).reshape(len(X), 4, -1)
+
+
+def training_set(lbm, n=256, seed=0, H_range=(64, 128), tol=1e-8, max_steps=2_000_000, check_every=200):
+    """Steady channel profiles computed by the scheme in one batch."""
+    cases = draw_channels(n, seed, H_range=H_range)
+    status, prof, xin, conv, secs = sweep.run_sweep(lbm, cases, max_steps=max_steps, tol=tol,
+                                                    check_every=check_every, autotune=False)
+    return dict(X=xin, Y=prof, converged=conv, seconds=secs, batch_steps=status["batch_steps"],
+                steps=status["steps"])
+
+
+def warm_fields(case, prof):
+    """(rho, u, T, Pi, q) of a channel from predicted profiles (u_x, T, Pi_xy (ny-1), q_y (ny-1))."""
+    p = case["params"]
+    nx, ny = p["nx"], p["ny"]
+    yq = np.linspace(0.0, 1.0, prof.shape[1])
+    y = np.arange(ny) / (ny - 1)
+    ux = np.interp(y, yq, prof[0])
+    T = np.interp(y, yq, prof[1])
+    Pxy = np.interp(y, yq, prof[2]) / (ny - 1)
+    qy = np.interp(y, yq, prof[3]) / (ny - 1)
+    T = np.maximum(T, 0.5)
+    # uniform pressure; the fluid rows (1..ny-2) carry the rest state's mass, the invariant
+    # that (with the walls) selects the steady state
+    rho = (1.0 / T) * (ny - 2) / np.sum(1.0 / T[1:-1])
+    col = lambda v: np.repeat(v[:, None], nx, axis=1)
+    R, Tt = col(rho), col(T)
+    u = np.stack([col(ux), np.zeros((ny, nx))])
+    Pi = np.stack([R * Tt, col(Pxy), R * Tt])
+    q = np.stack([np.zeros((ny, nx)), col(qy)])
+    return R, u, Tt, Pi, q
+
+
+def run_channels(lbm, cases, init, tol, max_steps, check_every):
+    """Runs the cases in one batch from `init(i, batch)`; per-instance steps to tol."""
+    bt = lbm.Batch([c["params"] for c in cases])
+    for i in range(len(cases)):
+        init(i, bt)
+    t0 = time.perf_counter()
+    done = bt.run(max_steps, tol=tol, check_every=check_every)
+    secs = time.perf_counter() - t0
+    steps, res, act = bt.status()
+    fields = [bt.moments(i) for i in range(len(cases))]
+    bt.close()
+    return dict(steps=steps, residual=res, converged=act == 0, seconds=secs, batch_steps=done), fields
+
+
+def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, max_steps=6_000_000, check_every=200,
+          train_H=(64, 128), iters=3000):
+    """Trains on steady channels, then compares warm start and rest start on held-out
+    4 x H channels: steps and batch wall time to residual `tol`, and the difference of
+    the two converged states."""
+    t0 = time.perf_counter()
+    ts = training_set(lbm, n_train, seed, H_range=train_H, tol=tol)
+    sur = Surrogate(lbm, seed=seed)
+    losses = sur.fit(ts["X"], ts["Y"], iters=iters)
+    t_train = time.perf_counter() - t0
+    test = draw_channels(n_test, seed + 1000, H=H)
+    X = np.array([c["inputs"] for c in test])
+    pred = sur.predict(X)
+    rest, f_rest = run_channels(lbm, test, lambda i, bt: bt.init(i, *sweep.initial_fields(test[i])), tol,
+                                max_steps, check_every)
+    warm, f_warm = run_channels(lbm, test, lambda i, bt: bt.init_neq(i, *warm_fields(test[i], pred[i])), tol,
+                                max_steps, check_every)
+    both = rest["converged"] & warm["converged"]
+    diff = []
+    for i in np.nonzero(both)[0]:
+        d = max(np.linalg.norm(f_warm[i][k] - f_rest[i][k]) / np.linalg.norm(f_rest[i][k]) for k in ("u", "T"))
+        diff.append(d)
+    # prediction error of the initial profiles against the converged rest-start state
+    perr = []
+    for i in range(n_test):
+        ref = sweep.profiles(f_rest[i])
+        perr.append(np.linalg.norm(pred[i][0] - ref[0]) / max(np.linalg.norm(ref[0]), 1e-30))
+    sr, sw = rest["steps"][both], warm["steps"][both]
+    return dict(
+        train=dict(n=n_train, H_range=list(train_H), converged=int(ts["converged"].sum()),
+                   sweep_seconds=ts["seconds"], batch_steps=ts["batch_steps"], losses=losses,
+                   seconds_total=t_train),
+        test=dict(n=n_test, H=H, tol=tol, both_converged=int(both.sum()),
+                  rest_converged=int(rest["converged"].sum()), warm_converged=int(warm["converged"].sum()),
+                  steps_rest_median=float(np.median(sr)) if len(sr) else None,
+                  steps_warm_median=float(np.median(sw)) if len(sw) else None,
+                  steps_rest_mean=float(np.mean(sr)) if len(sr) else None,
+                  steps_warm_mean=float(np.mean(sw)) if len(sw) else None,
+                  step_ratio_median=float(np.median(sw / sr)) if len(sr) else None,
+                  batch_seconds_rest=rest["seconds"], batch_seconds_warm=warm["seconds"],
+                  batch_steps_rest=rest["batch_steps"], batch_steps_warm=warm["batch_steps"],
+                  converged_state_diff_max=float(max(diff)) if diff else None,
+                  initial_u_profile_err_median=float(np.median(perr))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-train", type=int, default=256)
+    ap.add_argument("--n-test", type=int, default=256)
+    ap.add_argument("--H", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--max-steps", type=int, default=6_000_000)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    from . import build, lbm
+    build.build()
+    res = study(lbm, a.n_train, a.n_test, a.H, iters=a.iters, max_steps=a.max_steps)
+    s = json.dumps(res, indent=1, default=float)
+    print(s)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(s)
+
+
+if __name__ == "__main__":
+    main()
