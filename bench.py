@@ -208,6 +208,129 @@ def oracle_mlups(seconds=12.0, n=512):
             "sample": f"{n}x{n} thermal Taylor-Green sample of the workload, {steps} FP64 steps in {dt:.1f} s"}
 
 
+def bench_3d(torch, lbm, steps, warmup, peak, n=256):
+    """256^3 thermal Taylor-Green vortex on D3Q103 (FP32 and FP16 storage)."""
+    from paper_1611_02409_gb300 import inputs
+    fields = inputs.taylor_green_3d(n, U0=0.02, T_amp=0.01, noise=1e-6)
+    out = {"workload": f"3-D thermal Taylor-Green {n}^3 periodic, D3Q103, Pr=0.71, gamma=1.4, kappa=0.2, "
+                       f"tau=0.528655"}
+    for storage in ("fp32", "fp16"):
+        sim = lbm.Simulation(lattice=lbm.LBM_D3Q103, nx=n, ny=n, nz=n, storage=storage, **PARAMS)
+        sim.init(*fields)
+        total_ms, launch_ms, _ = time_steps(torch, lbm, sim, steps, warmup, 1)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        b_cell = 2 * 103 * 2 * (4 if storage == "fp32" else 2)
+        ach = b_cell * n ** 3 / (launch_ms * 1e-3) / 1e9
+        out[storage] = {"mlups": n ** 3 * steps / (total_ms * 1e-3) / 1e6, "launch_ms": launch_ms,
+                        "achieved_gbs": ach, "frac": ach / peak, "algorithmic_bytes_per_cell": b_cell,
+                        "steps": steps}
+    out["accuracy"] = accuracy_3d(lbm)
+    return out
+
+
+def accuracy_3d(lbm, n=32, steps=100):
+    """Field errors of FP32 and FP16 storage against the FP64 oracle on an n^3 copy of the
+    3-D workload (same parameters and field shape)."""
+    from oracle import oracle as O
+    from paper_1611_02409_gb300 import inputs
+    fields = inputs.taylor_green_3d(n, U0=0.02, T_amp=0.01, noise=1e-6)
+    o = O.Sim(O.D3Q103, nx=n, ny=n, nz=n, **PARAMS)
+    o.init(*fields)
+    o.step(steps)
+    mo = o.moments()
+    o.close()
+    out = {"case": f"3-D thermal Taylor-Green {n}^3, {steps} steps"}
+    for storage in ("fp32", "fp16"):
+        sim = lbm.Simulation(lattice=lbm.LBM_D3Q103, nx=n, ny=n, nz=n, storage=storage, **PARAMS)
+        sim.init(*fields)
+        sim.step(steps)
+        mg = sim.moments()
+        sim.close()
+        errs = {k: float(np.linalg.norm((mg[k] - mo[k]).ravel()) / np.linalg.norm(mo[k].ravel()))
+                for k in ("rho", "u", "T")}
+        errs["max_rel"] = max(errs.values())
+        out[storage] = errs
+    return out
+
+
+def bench_batch(torch, lbm, steps):
+    """The 512-instance sweep (256 Taylor-Green squares + 256 Couette channels) in one
+    batch: tile autotuned, then `steps` graph-replayed steps timed on the device."""
+    from paper_1611_02409_gb300 import sweep
+    cases = sweep.draw_instances()
+    bt = lbm.Batch([c["params"] for c in cases])
+    tile = bt.autotune(10)
+    for i, c in enumerate(cases):
+        bt.init(i, *sweep.initial_fields(c))
+    bt.run(100, tol=0.0, check_every=100)  # warm-up window (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = bt.run(steps, tol=0.0, check_every=100)
+    secs = time.perf_counter() - t0
+    ncomp = sum(c["params"]["nx"] * (c["params"]["ny"] - (2 if c["kind"] == "channel" else 0)) for c in cases)
+    bt.close()
+    return {"workload": "512 instances: 256 periodic thermal Taylor-Green squares (side 64..512) + 256 thermal "
+                        "Couette channels 4 x H (H 64..512), seeded Pr, gamma, tau, wall Mach, dT; D2Q37 FP32",
+            "cells": ncomp, "steps": done, "tile": tile, "seconds": secs,
+            "mlups": ncomp * done / secs / 1e6, "timing": "host wall clock around graph replays, synchronised"}
+
+
+def bench_couette(lbm):
+    """The Pr x gamma thermal Couette grid (4 x 256, U = 0.05, T 1.0 / 1.02), one batch:
+    steps to residual 1e-8, then nine decay times of the slowest thermal mode more; u and
+    T profiles against the analytic steady solution (Eq. CouetteDi3, unequal walls)."""
+    from paper_1611_02409_gb300 import sweep
+    cases = sweep.couette_grid()
+    H = cases[0]["params"]["ny"]
+    nu = 0.02
+    settle = int(9 * (H - 1) ** 2 / (np.pi ** 2 * nu / max(sweep.COUETTE_PR)))
+    out = sweep.run_couette(lbm, cases, tol=1e-8, settle_steps=settle, check_every=1000)
+    eta = np.arange(H) / (H - 1)
+    rows = []
+    for i, c in enumerate(cases):
+        Pr, gamma, U, _, dT = c["inputs"]
+        heat = Pr * U ** 2 / (2 + 2.0 / (gamma - 1.0) - 2.0 + 2)
+        T_an = 1.0 + dT * eta + heat * eta * (1 - eta)
+        err = lambda p: (float(np.abs(p[0] - U * eta).max() / U), float(np.abs(p[1] - T_an).max() / (heat / 4)))
+        eu8, eT8 = err(out["profiles_at_tol"][i])
+        eu, eT = err(out["profiles_settled"][i])
+        rows.append(dict(Pr=float(Pr), gamma=float(gamma), steps_to_1e8=int(out["steps_to_tol"][i]),
+                         u_err_at_1e8=eu8, T_err_at_1e8=eT8, u_err=eu, T_err=eT))
+    return {"workload": "thermal Couette 4x256, top wall U=0.05 T=1.02, bottom T=1.0, tau=0.528655, "
+                        "Pr x gamma = {0.5,0.71,1,2} x {1.3,1.4,1.67}, FP32, one batch",
+            "settle_steps": settle, "seconds_to_1e8": out["seconds_to_tol"], "seconds_settle": out["seconds_settle"],
+            "errors": "u: max|u - U eta| / U; T: max|T - T_analytic| / (peak viscous heating Pr U^2 / (4 (D+N_f+2)))",
+            "max_u_err": max(r["u_err"] for r in rows), "max_T_err": max(r["T_err"] for r in rows), "cases": rows}
+
+
+def bench_warm_start(lbm):
+    """The learned warm start: surrogate trained on 256 steady channels (H 64..128), then
+    256 held-out 4 x 256 channels from rest and from its prediction, to residual 1e-8."""
+    from paper_1611_02409_gb300 import surrogate
+    res, _ = surrogate.study(lbm)
+    t = res["test"]
+    return {"workload": "256 held-out thermal Couette channels 4x256, seeded Pr, gamma, Ma, tau, dT; surrogate "
+                        "5-512-512-512-512-1024 trained on 256 channels of height 64..128 by the lbm_mlp kernels",
+            "steps_rest_median": t["steps_rest_median"], "steps_warm_median": t["steps_warm_median"],
+            "step_ratio_median": t["step_ratio_median"], "batch_seconds_rest": t["batch_seconds_rest"],
+            "batch_seconds_warm": t["batch_seconds_warm"], "converged": [t["rest_converged"], t["warm_converged"]],
+            "state_diff_at_1e8": t["state_diff_at_tol"], "state_diff_at_1e9": t["state_diff_at_tol_fine"],
+            "train_seconds": res["train"]["seconds_total"], "final_loss": res["train"]["losses"][-1][1]}
+
+
+def _extra(out, name, fn):
+    """One extra measurement; its failure is recorded, not raised."""
+    t0 = time.perf_counter()
+    try:
+        out[name] = fn()
+    except Exception as e:  # the headline line must still print
+        out[name] = {"error": f"{type(e).__name__}: {e}"}
+    if isinstance(out[name], dict):
+        out[name]["wall_seconds"] = time.perf_counter() - t0
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -297,10 +420,14 @@ def run_ours(args):
     h2d = 8 * cells * 4
     d2h = 8 * cells * 4
     extra = {}
-    if rank == 0:
-        extra["accuracy"] = accuracy_vs_oracle(lbm)
-        if ws == 1:
-            extra["cpu_baseline"] = oracle_mlups()
+    if ws == 1:
+        # the other configurations, measured at one GPU only (they hold no other rank)
+        _extra(extra, "accuracy", lambda: accuracy_vs_oracle(lbm))
+        _extra(extra, "d3q103_256", lambda: bench_3d(torch, lbm, max(args.steps // 8, 20), args.warmup, peak))
+        _extra(extra, "batched_sweep", lambda: bench_batch(torch, lbm, max(args.steps // 2, 100)))
+        _extra(extra, "couette_grid", lambda: bench_couette(lbm))
+        _extra(extra, "warm_start", lambda: bench_warm_start(lbm))
+        extra["cpu_baseline"] = oracle_mlups()
     if rank != 0:
         return
     r32 = results["fp32"]

@@ -71,6 +71,8 @@ extern "C" {
 #define LBM_KERNEL_DIRECT 1  /* one cell per thread, populations gathered from HBM     */
 #define LBM_KERNEL_STAGED 2  /* persistent tiles staged in shared memory by bulk
                                 asynchronous copies (D = 2, nx a multiple of 128)      */
+#define LBM_KERNEL_PAIRED 3  /* two neighbouring cells per thread in packed FP32 pairs
+                                (D = 2, FP16 or BF16 storage, nx even)                 */
 
 /* memory space of field pointers */
 #define LBM_MEM_DEVICE 0
@@ -222,6 +224,12 @@ int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int 
 /* Per-instance status (host arrays of n entries, any may be NULL): steps taken, last
  * residual (infinity before the second check), active flag (0 once converged). */
 int lbm_batch_status(lbm_batch *b, int *steps, double *residual, int *active);
+
+/* Re-activates instance i (every instance when i < 0) without touching its populations
+ * or step count, so a finished batch can continue to a tighter tolerance; its next
+ * residual check takes a fresh snapshot.  An instance whose residual is NaN (a diverged
+ * run, deactivated at its check) stays inactive.  Synchronises the batch's stream. */
+int lbm_batch_activate(lbm_batch *b, int i);
 
 /* Fields of instance i (as lbm_moments). */
 int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u, double *T, double *Pi, double *q, int mem);

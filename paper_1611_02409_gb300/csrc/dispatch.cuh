@@ -69,6 +69,8 @@ template <int LAT, int ST> struct Launch {
         return Lattice<LAT>::D == 2 && c.nx % TileGeom<ST>::TW == 0 && c.d_err != nullptr;
     }
     static bool tma_ok(const Ctx &c) { return c.kernel == 2 && staged_ok(c); }
+    // two cells per thread: 2-D, 16-bit storage, even rows
+    static bool paired_ok(const Ctx &c) { return Lattice<LAT>::D == 2 && ST != ST_FP32 && c.nx % 2 == 0; }
     template <bool W> static void step_tma(const Ctx &c, const KParams<LAT> &kp, const void *src, void *dst,
                                            cudaStream_t st)
     {
@@ -92,6 +94,17 @@ template <int LAT, int ST> struct Launch {
             if (tma_ok(c)) {
                 if (c.walls) step_tma<true>(c, kp, src, dst, st);
                 else step_tma<false>(c, kp, src, dst, st);
+                return;
+            }
+        }
+        if constexpr (Lattice<LAT>::D == 2 && ST != ST_FP32) {
+            if (c.kernel == 3 && paired_ok(c)) {
+                const dim3 grid((c.nx / 2 + kTx - 1) / kTx, kp.ny_comp, 1);
+                const int sy = c.ny < 4;
+                if (c.walls)
+                    k_stream_collide_pair<LAT, ST, true><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sy);
+                else
+                    k_stream_collide_pair<LAT, ST, false><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sy);
                 return;
             }
         }
@@ -147,6 +160,7 @@ template <int LAT, int ST> Ops make_ops_st()
     o.get_pops = &Launch<LAT, ST>::get_pops;
     o.set_pops = &Launch<LAT, ST>::set_pops;
     o.staged_ok = &Launch<LAT, ST>::staged_ok;
+    o.paired_ok = &Launch<LAT, ST>::paired_ok;
     return o;
 }
 

@@ -6,6 +6,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "physics.cuh"
 
 namespace lbm {
@@ -32,58 +34,81 @@ __device__ __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, i
     return ((long long)z * kp.nys + ys) * kp.nx + x;
 }
 
+// Byte offsets of the 2Q destination planes from a cell's set-0 plane-0 address: a
+// per-population table (the single-domain kernels' constant-bank offsets) ...
+struct TableOff {
+    const long long *soff;
+    __device__ __forceinline__ long long operator()(int I) const { return soff[I]; }
+};
+// ... or the plane stride (batched instances: per-instance planes, 32-bit offsets).
+template <int ELEM> struct StrideOff {
+    int plane;
+    __device__ __forceinline__ long long operator()(int I) const { return (long long)(I * plane) * ELEM; }
+};
+
 // Relax population I of a cell and store it: s' = s + omega(G~/w - s), same for t.
-// `cell` is the destination cell's address in set 0 plane 0; soff the planes' byte offsets.
-template <int LAT, int ST>
-__device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ cell, const long long *soff,
-                                            int I, float om, const EqScal &z, float q, float s, float t)
+// `cell` is the destination cell's address in set 0 plane 0; off(I) the planes' byte offsets.
+// With V = f2 (two neighbouring cells, 16-bit storage) both lanes are relaxed by packed
+// FMAs and stored as one 32-bit word at the first cell's address.
+template <int LAT, int ST, class Off, class V>
+__device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ cell, const Off &off, int I,
+                                            float om, const EqScalT<V> &z, V q, V s, V t)
 {
     using T = typename Storage<ST>::T;
     constexpr int Q = Lattice<LAT>::Q;
     char *b = reinterpret_cast<char *>(cell);
-    if constexpr (ST == ST_FP32) {
+    if constexpr (std::is_same<V, f2>::value) {
+        static_assert(ST != ST_FP32, "paired cells use 16-bit storage");
+        Storage<ST>::st2(reinterpret_cast<T *>(b + off(I)), vfma(f2(z.om1), s, vfma(f2(om), q, z.wdrho)));
+        Storage<ST>::st2(reinterpret_cast<T *>(b + off(Q + I)), vfma(f2(z.om1), t, vfma(z.whr, q, z.whb)));
+    } else if constexpr (ST == ST_FP32) {
         // difference form: the non-equilibrium part G~/w - s is formed exactly
         const float Gs = z.drho + q;
         const float Ht = fmaf(z.hr, q, z.hb);
-        Storage<ST>::st(reinterpret_cast<T *>(b + soff[I]), fmaf(om, Gs - s, s));
-        Storage<ST>::st(reinterpret_cast<T *>(b + soff[Q + I]), fmaf(om, Ht - t, t));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), fmaf(om, Gs - s, s));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), fmaf(om, Ht - t, t));
     } else {
         // (1 - omega) s + omega G~/w in two FMAs (z carries omega-scaled terms); its extra
         // FP32 rounding is far below the 16-bit storage rounding
-        Storage<ST>::st(reinterpret_cast<T *>(b + soff[I]), fmaf(z.om1, s, fmaf(om, q, z.wdrho)));
-        Storage<ST>::st(reinterpret_cast<T *>(b + soff[Q + I]), fmaf(z.om1, t, fmaf(z.whr, q, z.whb)));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), fmaf(z.om1, s, fmaf(om, q, z.wdrho)));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), fmaf(z.om1, t, fmaf(z.whr, q, z.whb)));
     }
 }
 
 // Collide one cell's streamed populations (accessor `pop`) and store them at offset o.
-template <int LAT, int ST, class Pop>
+template <int LAT, int ST, class Pop, class Off = TableOff>
 __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop &pop,
-                                              typename Storage<ST>::T *__restrict__ dst, long long o)
+                                              typename Storage<ST>::T *__restrict__ dst, long long o,
+                                              const Off &off = Off{nullptr})
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     constexpr bool PRECISE = ST == ST_FP32;
-    RawMoments<D> m;
+    using V = typename Pop::V;
+    RawMoments<D, V> m;
     raw_moments<LAT, PRECISE>(kp, pop, m);
-    CellState<D> c;
+    CellState<D, V> c;
     cell_state<LAT>(kp, m, c);
-    EqState<D> e;
+    EqState<D, V> e;
     es_state<LAT>(kp, c, e);
-    PolyCoef<D> pc;
+    PolyCoef<D, V> pc;
     poly_coeffs<D>(e, kp.r, kp.R2_hi, PRECISE ? kp.R2_lo : 0.f, pc);
-    EqScal z = eq_scalars<D>(e, kp.halfNf);
+    EqScalT<V> z = eq_scalars<D>(e, kp.halfNf);
     z.om1 = 1.f - kp.omega;
     z.wdrho = kp.omega * z.drho;
     z.whb = kp.omega * z.hb;
     z.whr = kp.omega * z.hr;
     typename Storage<ST>::T *cell = dst + o;
-    relax_store<LAT, ST>(cell, kp.soff, 0, kp.omega, z, pc.k[0], pop.template sv<0>(), pop.template tv<0>());
+    Off so = off;
+    if constexpr (std::is_same<Off, TableOff>::value) so.soff = kp.soff;
+    pop.refresh();
+    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], pop.template sv<0>(), pop.template tv<0>());
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
-        float E, O;
+        V E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
-        relax_store<LAT, ST>(cell, kp.soff, I, kp.omega, z, E + O, pop.template sv<I>(), pop.template tv<I>());
-        relax_store<LAT, ST>(cell, kp.soff, I + 1, kp.omega, z, E - O, pop.template sv<I + 1>(),
+        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, pop.template sv<I>(), pop.template tv<I>());
+        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, pop.template sv<I + 1>(),
                              pop.template tv<I + 1>());
     });
 }
@@ -149,6 +174,93 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
         t[i] = S::cvt(rt[i]);
     }
     collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o);
+}
+
+// Two neighbouring cells' stored 16-bit values, one 32-bit word per population (low
+// half: the even cell).  Values are converted to FP32 pairs where they are used; refresh()
+// makes the words opaque between the moment sums and the relaxation, so the converted
+// pairs are formed again there instead of being held in registers across the cell.
+template <int ST, int Q> struct RawPop2 {
+    using V = f2;
+    uint32_t *s, *t;
+    template <int I> __device__ __forceinline__ f2 sv() const { return Storage<ST>::cvt2(s[I]); }
+    template <int I> __device__ __forceinline__ f2 tv() const { return Storage<ST>::cvt2(t[I]); }
+    __device__ __forceinline__ void refresh() const
+    {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            asm volatile("" : "+r"(s[i]));
+            asm volatile("" : "+r"(t[i]));
+        }
+    }
+};
+
+// 32-bit word of the 16-bit values at element offsets e and e + 1 from p, for an odd e:
+// the two aligned words around them, then a byte permute.
+__device__ __forceinline__ uint32_t ld_pair_odd(const char *p)
+{
+    const uint32_t w0 = __ldg(reinterpret_cast<const unsigned int *>(p - 2));
+    const uint32_t w1 = __ldg(reinterpret_cast<const unsigned int *>(p + 2));
+    return __byte_perm(w0, w1, 0x5432);
+}
+
+// The fused step for 16-bit storage on the 2-D lattice with two neighbouring cells
+// (x, x + 1; x even) per thread: each population's two source values come in one 32-bit
+// load when c_x is even (the pair stays word-aligned) and in two loads and a byte permute
+// when it is odd; the collision of both cells runs in packed FP32 pairs (one FFMA2 per
+// pair of FMAs) and both results leave in one 32-bit store.  Needs nx even.  Per cell
+// the arithmetic is the one-cell kernel's non-compensated FP32 form, evaluated per lane.
+template <int LAT, int ST, bool WALLS>
+__global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename Storage<ST>::T *__restrict__ src,
+                                                               typename Storage<ST>::T *__restrict__ dst,
+                                                               const KParams<LAT> kp, int small_y)
+{
+    static_assert(Lattice<LAT>::D == 2 && ST != ST_FP32, "paired cells: 2-D lattice, 16-bit storage");
+    constexpr int Q = Lattice<LAT>::Q;
+    using T = typename Storage<ST>::T;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y + kp.y0;
+    const long long o = cell_index<LAT>(kp, x, y + kp.gh, 0);
+    // a block whose every source word (x - c_x - 1 .. x + 1 - c_x + 1, |c_x| <= 3) lies inside
+    // the row gathers at the fixed byte offsets
+    const int xb = 2 * blockIdx.x * blockDim.x;
+    bool interior = xb >= 4 && xb + 2 * (int)blockDim.x + 4 <= kp.nx;
+    if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
+    uint32_t rs[Q], rt[Q];
+    if (interior) {
+        const char *base = reinterpret_cast<const char *>(src + o);
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            constexpr int cx = cv<LAT, I, 0>();
+            if constexpr (cx % 2 == 0) {
+                rs[I] = __ldg(reinterpret_cast<const unsigned int *>(base + kp.goff[I]));
+                rt[I] = __ldg(reinterpret_cast<const unsigned int *>(base + kp.goff[Q + I]));
+            } else {
+                rs[I] = ld_pair_odd(base + kp.goff[I]);
+                rt[I] = ld_pair_odd(base + kp.goff[Q + I]);
+            }
+        });
+    } else {
+        const unsigned short *sp = reinterpret_cast<const unsigned short *>(src);
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>();
+            // nx >= 2 is even here, so x - c_x and x + 1 - c_x wrap with one correction
+            // each once |c_x| <= nx; smaller rows take the modulo path
+            const bool sx = kp.nx < 4;
+            const int x0 = wrap_sub<cx>(x, kp.nx, sx), x1 = wrap_sub<cx>(x + 1, kp.nx, sx);
+            int ys;
+            if constexpr (WALLS) ys = y - cy + kp.gh;
+            else ys = wrap_sub<cy>(y, kp.ny, small_y);
+            const long long row = (long long)ys * kp.nx;
+            const long long ps = (long long)I * kp.plane + row, pt = (long long)(Q + I) * kp.plane + row;
+            rs[I] = (uint32_t)__ldg(sp + ps + x0) | ((uint32_t)__ldg(sp + ps + x1) << 16);
+            rt[I] = (uint32_t)__ldg(sp + pt + x0) | ((uint32_t)__ldg(sp + pt + x1) << 16);
+        });
+    }
+    asm volatile("" ::: "memory");
+    collide_store<LAT, ST>(kp, RawPop2<ST, Q>{rs, rt}, dst, o);
 }
 
 // Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].

@@ -515,7 +515,9 @@ int lbm_set_kernel(lbm_handle *h, int variant)
     if (variant == LBM_KERNEL_AUTO) variant = LBM_KERNEL_DIRECT;
     if (variant == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx))
         return set_err(h, LBM_ERR_ARG, "staged kernel needs D = 2 and nx a multiple of 128");
-    if (variant != LBM_KERNEL_DIRECT && variant != LBM_KERNEL_STAGED) return set_err(h, LBM_ERR_ARG, "bad variant");
+    if (variant == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx))
+        return set_err(h, LBM_ERR_ARG, "paired kernel needs D = 2, 16-bit storage and nx even");
+    if (variant < LBM_KERNEL_DIRECT || variant > LBM_KERNEL_PAIRED) return set_err(h, LBM_ERR_ARG, "bad variant");
     h->ctx.kernel = variant;
     return LBM_OK;
 }
@@ -528,8 +530,9 @@ int lbm_autotune(lbm_handle *h, int steps, int *chosen)
     LBM_CK(h, cudaEventCreate(&e1));
     float best = -1.f;
     int best_v = LBM_KERNEL_DIRECT;
-    for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_STAGED; ++v) {
+    for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_PAIRED; ++v) {
         if (v == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx)) continue;
+        if (v == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx)) continue;
         h->ctx.kernel = v;
         int rc = lbm_step(h, 2);
         if (rc) return rc;

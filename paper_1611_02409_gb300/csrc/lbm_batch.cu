@@ -6,6 +6,7 @@
 // wall_column), so a batched instance reproduces lbm_step bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -58,45 +59,58 @@ __global__ void __launch_bounds__(kThreads, 4) k_bstep(const Inst *__restrict__ 
         const int cur = d.cur, walls = d.walls, ncomp = d.ncomp;
         const float *src = arena + d.buf[cur];
         float *dst = arena + d.buf[cur ^ 1];
-        const int sx = kp.nx < 4, sy = kp.ny < 4;
+        const int nx = kp.nx, ny = kp.ny, gh = kp.gh, plane = (int)kp.plane;
+        const int sx = nx < 4, sy = ny < 4;
 #pragma unroll 1
         for (int c = 0; c < CPT; ++c) {
-            const long long cell = (long long)it.y * (kThreads * CPT) + c * kThreads + threadIdx.x;
+            const int cell = it.y * (kThreads * CPT) + c * kThreads + threadIdx.x;
             if (cell >= ncomp) break;
-            const int x = (int)(cell % kp.nx);
-            const int y = kp.y0 + (int)(cell / kp.nx);
+            const int x = cell % nx;
+            const int y = kp.y0 + cell / nx;
+            // the plane stride is opaque per cell, so the 2Q products I * plane are formed
+            // where they are used instead of being hoisted out of the loop into registers
+            int pl = plane;
+            asm volatile("" : "+r"(pl));
+            // source rows (as element offsets) and columns of the 7 stencil displacements
+            // -3..3; an instance's 2Q planes span < 2^31 elements
+            int rowo[7], col[7];
+            static_for<0, 7>([&](auto KK) {
+                constexpr int C = decltype(KK)::value - 3;
+                const int ys = walls ? y - C + gh : wrap_sub<C>(y, ny, sy);
+                rowo[KK] = ys * nx;
+                col[KK] = wrap_sub<C>(x, nx, sx);
+            });
             float s[Q], t[Q];
             static_for<0, Q>([&](auto II) {
                 constexpr int I = decltype(II)::value;
                 constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>();
-                const int xs = wrap_sub<cx>(x, kp.nx, sx);
-                const int ys = walls ? y - cy + kp.gh : wrap_sub<cy>(y, kp.ny, sy);
-                const long long idx = (long long)ys * kp.nx + xs;
-                s[I] = __ldg(src + (long long)I * kp.plane + idx);
-                t[I] = __ldg(src + (long long)(Q + I) * kp.plane + idx);
+                const int idx = rowo[cy + 3] + col[cx + 3];
+                s[I] = __ldg(src + (I * pl + idx));
+                t[I] = __ldg(src + ((Q + I) * pl + idx));
             });
-            const long long o = (long long)(y + kp.gh) * kp.nx + x;
-            collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o);
+            const int o = (y + gh) * nx + x;
+            collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o, StrideOff<4>{pl});
         }
     }
 }
 
-// Walls of every active channel on its freshly written buffer (before the flip).
-__global__ void k_bwalls(const Inst *__restrict__ inst, const KP *__restrict__ kps, float *arena)
+// Walls of every active channel on its freshly written buffer, then the buffer flip and
+// step count of every active instance: one block per instance, which touches only its
+// own buffer and record, so walls and flip need no ordering across blocks.
+__global__ void k_bwalls_flip(Inst *__restrict__ inst, const KP *__restrict__ kps, float *arena)
 {
-    const Inst &d = inst[blockIdx.x];
-    if (!d.walls || !d.active) return;
-    const KP &kp = kps[blockIdx.x];
-    float *buf = arena + d.buf[d.cur ^ 1];
-    for (int j = threadIdx.x; j < 2 * kp.nx; j += blockDim.x) wall_column<LAT, ST>(buf, kp, d.wp, j % kp.nx, j / kp.nx);
-}
-
-__global__ void k_bflip(Inst *inst, int n)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && inst[i].active) {
-        inst[i].cur ^= 1;
-        inst[i].steps += 1;
+    Inst &d = inst[blockIdx.x];
+    if (!d.active) return;
+    if (d.walls) {
+        const KP &kp = kps[blockIdx.x];
+        float *buf = arena + d.buf[d.cur ^ 1];
+        for (int j = threadIdx.x; j < 2 * kp.nx; j += blockDim.x)
+            wall_column<LAT, ST>(buf, kp, d.wp, j % kp.nx, j / kp.nx);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        d.cur ^= 1;
+        d.steps += 1;
     }
 }
 
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(256) k_bresid(Inst *inst, const KP *__restrict
             const double ru = t[1] > 0 ? sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
             const double rT = t[3] > 0 ? sqrt(t[2] / t[3]) : 0.0;
             d.residual = fmax(ru, rT) / m;
-            if (d.residual < tol) d.active = 0;
+            if (d.residual < tol || isnan(d.residual)) d.active = 0;  // converged, or diverged
         } else {
             d.residual = INFINITY;
             d.have_snap = 1;
@@ -243,15 +257,18 @@ int step_grid(int tile, int num_sms)
 void launch_window(lbm_batch *b, int window, double tol, int tile)
 {
     const int n = b->n;
-    const int grid = step_grid(tile, b->num_sms);
+    // persistent grid: the resident blocks of every SM, but no more than the work items
+    // of all instances (the work list only shrinks as instances converge)
+    long long items = 0;
+    for (const Inst &in : b->inst0) items += (in.ncomp + tile - 1) / tile;
+    const int grid = (int)std::max(1LL, std::min((long long)step_grid(tile, b->num_sms), items));
     k_bwork_offsets<<<1, 32, 0, b->stream>>>(b->d_inst, n, tile, b->d_off, b->d_nwork);
     k_bwork_fill<<<n, 128, 0, b->stream>>>(b->d_inst, tile, b->d_off, b->d_work);
     for (int s = 0; s < window; ++s) {
         if (tile == 512) k_bstep<4><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
         else if (tile == 256) k_bstep<2><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
         else k_bstep<1><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
-        k_bwalls<<<n, 64, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena);
-        k_bflip<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_inst, n);
+        k_bwalls_flip<<<n, 64, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena);
     }
     k_bresid<<<n, 256, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena, window, tol);
     k_bcount<<<1, 32, 0, b->stream>>>(b->d_inst, n, b->d_nwork);
@@ -454,6 +471,23 @@ int lbm_batch_status(lbm_batch *b, int *steps, double *residual, int *active)
         if (residual) residual[i] = h[i].residual;
         if (active) active[i] = h[i].active;
     }
+    return LBM_OK;
+}
+
+int lbm_batch_activate(lbm_batch *b, int i)
+{
+    if (!b || i >= b->n) return bfail(b, LBM_ERR_ARG, "bad instance");
+    std::vector<Inst> h(b->n);
+    LBM_BCK(b, cudaMemcpyAsync(h.data(), b->d_inst, sizeof(Inst) * b->n, cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCK(b, cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < b->n; ++k) {
+        if ((i >= 0 && k != i) || std::isnan(h[k].residual)) continue;
+        h[k].active = 1;
+        h[k].have_snap = 0;
+        h[k].residual = std::numeric_limits<double>::infinity();
+    }
+    LBM_BCK(b, cudaMemcpyAsync(b->d_inst, h.data(), sizeof(Inst) * b->n, cudaMemcpyHostToDevice, b->stream));
+    LBM_BCK(b, cudaStreamSynchronize(b->stream));
     return LBM_OK;
 }
 

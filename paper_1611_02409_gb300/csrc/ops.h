@@ -29,6 +29,7 @@ struct Ops {
     void (*get_pops)(const Ctx &, const void *buf, double *g, double *h, cudaStream_t);
     void (*set_pops)(const Ctx &, void *buf, const double *g, const double *h, cudaStream_t);
     bool (*staged_ok)(const Ctx &);
+    bool (*paired_ok)(const Ctx &);
 };
 
 Ops ops_d2q37(int storage);

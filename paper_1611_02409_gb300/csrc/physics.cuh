@@ -19,8 +19,12 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <type_traits>
 
 #include "lattice.cuh"
+#include "vec2.cuh"
 
 namespace lbm {
 
@@ -47,6 +51,20 @@ template <> struct Storage<ST_FP16> {
     static __device__ __forceinline__ float cvt(Raw r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ float ld(const T *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v))); }
+    // two neighbouring cells' values in one 32-bit word (low half: the first cell)
+    static __device__ __forceinline__ f2 cvt2(uint32_t r)
+    {
+        __half2 h;
+        memcpy(&h, &r, 4);
+        return as_f2(__half22float2(h));
+    }
+    static __device__ __forceinline__ void st2(T *p, f2 v)
+    {
+        const __half2 h = __float22half2_rn(as_float2(v));
+        uint32_t r;
+        memcpy(&r, &h, 4);
+        __stcs(reinterpret_cast<unsigned int *>(p), r);
+    }
 };
 template <> struct Storage<ST_BF16> {
     using T = __nv_bfloat16;
@@ -58,6 +76,19 @@ template <> struct Storage<ST_BF16> {
     static __device__ __forceinline__ float cvt(Raw r) { return __bfloat162float(__ushort_as_bfloat16(r)); }
     static __device__ __forceinline__ float ld(const T *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v))); }
+    static __device__ __forceinline__ f2 cvt2(uint32_t r)
+    {
+        __nv_bfloat162 h;
+        memcpy(&h, &r, 4);
+        return as_f2(__bfloat1622float2(h));
+    }
+    static __device__ __forceinline__ void st2(T *p, f2 v)
+    {
+        const __nv_bfloat162 h = __float22bfloat162_rn(as_float2(v));
+        uint32_t r;
+        memcpy(&r, &h, 4);
+        __stcs(reinterpret_cast<unsigned int *>(p), r);
+    }
 };
 
 // Per-launch parameters (passed by value; read from the constant bank).
@@ -92,30 +123,31 @@ template <int LAT> struct KParams {
 // equilibrium's conserved moments come out of the lattice sums without a division by
 // rho: a rounded 1/rho is nearly the same in every cell of a smooth flow, and rho (1/rho)
 // != 1 would scale momentum by the same factor every step.
-template <int D> struct EqState {
-    float drho, rho, inv_rho;
-    float J[D];           // rho v, v = u / r the lattice-unit velocity
-    float u[D];           // velocity (xi units), for second-order terms
-    float X[D][D];        // rho (A + u u), A = Lambda - delta
-    float A[D][D];        // A, for second-order terms
-    float rth_rel;        // rho (T_rel - 1)
-    float th_rel;         // T_rel - 1
+// V = float for one cell, f2 for two neighbouring cells in the lanes of packed FP32 pairs.
+template <int D, class V = float> struct EqState {
+    V drho, rho, inv_rho;
+    V J[D];               // rho v, v = u / r the lattice-unit velocity
+    V u[D];               // velocity (xi units), for second-order terms
+    V X[D][D];            // rho (A + u u), A = Lambda - delta
+    V A[D][D];            // A, for second-order terms
+    V rth_rel;            // rho (T_rel - 1)
+    V th_rel;             // T_rel - 1
 };
 
 // Monomial coefficients of q(xi) = P(xi) - 1 at xi = r c, for the state s.
-template <int D> struct PolyCoef {
+template <int D, class V = float> struct PolyCoef {
     static constexpr int K = Monos<D>::K;
-    float k[K];
+    V k[K];
 };
 
-template <int D>
-__device__ __forceinline__ float c3_of(const float (&A)[D][D], const float (&u)[D], int a, int b, int c)
+template <int D, class V>
+__device__ __forceinline__ V c3_of(const V (&A)[D][D], const V (&u)[D], int a, int b, int c)
 {
     return A[a][b] * u[c] + A[a][c] * u[b] + A[b][c] * u[a] + u[a] * u[b] * u[c];
 }
 
-template <int D>
-__device__ __forceinline__ float c4_of(const float (&A)[D][D], const float (&u)[D], int a, int b, int c, int d)
+template <int D, class V>
+__device__ __forceinline__ V c4_of(const V (&A)[D][D], const V (&u)[D], int a, int b, int c, int d)
 {
     return A[a][b] * A[c][d] + A[a][c] * A[b][d] + A[a][d] * A[b][c]
          + A[a][b] * u[c] * u[d] + A[a][c] * u[b] * u[d] + A[a][d] * u[b] * u[c]
@@ -124,21 +156,21 @@ __device__ __forceinline__ float c4_of(const float (&A)[D][D], const float (&u)[
 }
 
 // Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!.
-template <int D>
-__device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float R2_hi, float R2_lo,
-                                            PolyCoef<D> &pc)
+template <int D, class V>
+__device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, float R2_hi, float R2_lo,
+                                            PolyCoef<D, V> &pc)
 {
     const auto &A = s.A;
     const auto &u = s.u;
-    const float rho = s.rho;
-    float trA = 0.f, u2 = 0.f, trA2 = 0.f, uAu = 0.f, trX = 0.f;
-    float Au[D], AJ[D], A2[D][D];
+    const V rho = s.rho;
+    V trA = 0.f, u2 = 0.f, trA2 = 0.f, uAu = 0.f, trX = 0.f;
+    V Au[D], AJ[D], A2[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         trA += A[a][a];
         trX += s.X[a][a];
         u2 += u[a] * u[a];
-        float t = 0.f, tj = 0.f;
+        V t = 0.f, tj = 0.f;
 #pragma unroll
         for (int b = 0; b < D; ++b) {
             t += A[a][b] * u[b];
@@ -152,7 +184,7 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float 
         uAu += u[a] * Au[a];
 #pragma unroll
         for (int b = 0; b < D; ++b) {
-            float t = 0.f;
+            V t = 0.f;
 #pragma unroll
             for (int c = 0; c < D; ++c) t += A[a][c] * A[c][b];
             A2[a][b] = t;
@@ -160,16 +192,16 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float 
         }
     }
     // rho (C_0 - 1) = -rho tr a2 / 2 + rho tr^2 a4 / 8,  rho tr a2 = tr X
-    const float k0 = -0.5f * trX + 0.125f * rho * (trA * trA + 2.f * trA2 + 2.f * u2 * trA + 4.f * uAu + u2 * u2);
+    const V k0 = -0.5f * trX + 0.125f * rho * (trA * trA + 2.f * trA2 + 2.f * u2 * trA + 4.f * uAu + u2 * u2);
     // rho r C_1 = r^2 (J - (tr A J + 2 A J + u^2 J)/2)
-    float k1[D];
+    V k1[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float y = s.J[a] - 0.5f * (trA * s.J[a] + 2.f * AJ[a] + u2 * s.J[a]);
-        k1[a] = fmaf(R2_hi, y, R2_lo * y);
+        const V y = s.J[a] - 0.5f * (trA * s.J[a] + 2.f * AJ[a] + u2 * s.J[a]);
+        k1[a] = vfma(R2_hi, y, R2_lo * y);
     }
     // rho C_2 = X - rho tr a4 / 2 (the trace part is second order)
-    float c2[D][D];
+    V c2[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -184,26 +216,26 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D> &s, float r, float 
         constexpr float inv = (float)inv_alpha_factorial<D, K>();
         constexpr int i0 = mono_index<D, K>(0), i1 = mono_index<D, K>(1);
         constexpr int i2 = mono_index<D, K>(2), i3 = mono_index<D, K>(3);
-        float v;
+        V v;
         if constexpr (m == 0) v = k0;
         else if constexpr (m == 1) v = k1[i0];
         else if constexpr (m == 2) {
             // r^2 in hi + lo so that the mass and energy sums close on the same constant
-            const float x = inv * c2[i0][i1];
-            v = fmaf(R2_hi, x, R2_lo * x);
+            const V x = inv * c2[i0][i1];
+            v = vfma(R2_hi, x, R2_lo * x);
         }
-        else if constexpr (m == 3) v = r3 * inv * rho * c3_of<D>(A, u, i0, i1, i2);
-        else v = r4 * inv * rho * c4_of<D>(A, u, i0, i1, i2, i3);
+        else if constexpr (m == 3) v = r3 * inv * rho * c3_of<D, V>(A, u, i0, i1, i2);
+        else v = r4 * inv * rho * c4_of<D, V>(A, u, i0, i1, i2, i3);
         pc.k[K] = v;
     });
 }
 
 // Even and odd parts of q at velocity I (compile-time), q(c_I) = E + O, q(-c_I) = E - O.
-template <int LAT, int I>
-__device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D> &pc, float &E, float &O)
+template <int LAT, int I, class V>
+__device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D, V> &pc, V &E, V &O)
 {
     constexpr int D = Lattice<LAT>::D;
-    float e = 0.f, o = 0.f;
+    V e = 0.f, o = 0.f;
     static_for<0, Monos<D>::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
         constexpr int mv = mono_at<LAT, I, K>();
@@ -211,11 +243,11 @@ __device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D> &
             if constexpr (Monos<D>::M.deg[K] % 2 == 0) {
                 if constexpr (mv == 1) e += pc.k[K];
                 else if constexpr (mv == -1) e -= pc.k[K];
-                else e = fmaf((float)mv, pc.k[K], e);
+                else e = vfma(V((float)mv), pc.k[K], e);
             } else {
                 if constexpr (mv == 1) o += pc.k[K];
                 else if constexpr (mv == -1) o -= pc.k[K];
-                else o = fmaf((float)mv, pc.k[K], o);
+                else o = vfma(V((float)mv), pc.k[K], o);
             }
         }
     });
@@ -224,17 +256,21 @@ __device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D> &
 }
 
 // Raw deviation moments of one cell's populations (s = g~/w, t = h~/w).
-template <int D> struct RawMoments {
-    float drho;           // sum g~
-    float J[D];           // sum g~ c
-    float M[D][D];        // sum g~ c c
-    float H;              // sum h~
+template <int D, class V = float> struct RawMoments {
+    V drho;               // sum g~
+    V J[D];               // sum g~ c
+    V M[D][D];            // sum g~ c c
+    V H;                  // sum h~
 };
 
 // Population accessors: pop.template sv<I>() / tv<I>() return the scaled deviations s_I,
-// t_I of one cell (from registers, or from a shared-memory tile).
+// t_I of one cell (from registers, or from a shared-memory tile) as V; refresh() is
+// called between the moment sums and the relaxation (a no-op unless the accessor
+// re-converts stored values there instead of keeping them live).
 struct ArrayPop {
+    using V = float;
     const float *s, *t;
+    __device__ __forceinline__ void refresh() const {}
     template <int I> __device__ __forceinline__ float sv() const { return s[I]; }
     template <int I> __device__ __forceinline__ float tv() const { return t[I]; }
 };
@@ -243,17 +279,20 @@ struct ArrayPop {
 // 16-bit storage forms round every population to 2^-11 (FP16) or 2^-8 (BF16) each step,
 // far above these 1e-8 effects, and fold with the FP32 weights alone.
 template <int LAT, bool PRECISE = true, class Pop>
-__device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &pop, RawMoments<Lattice<LAT>::D> &m)
+__device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &pop,
+                                            RawMoments<Lattice<LAT>::D, typename Pop::V> &m)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
+    using V = typename Pop::V;
+    static_assert(!PRECISE || std::is_same<V, float>::value, "the compensated sums are scalar");
     constexpr int NM = 2 + D + D * (D + 1) / 2; // drho, H, J, M (upper triangle)
     // hi and lo accumulators of the weighted sums
-    float hi[NM], lo[NM];
+    V hi[NM], lo[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) hi[k] = lo[k] = 0.f;
     // unweighted partial sums of the current shell (velocities come shell by shell)
-    float part[NM];
+    V part[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) part[k] = 0.f;
     part[0] = pop.template sv<0>();
@@ -267,28 +306,29 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
         if constexpr (!PRECISE) {
 #pragma unroll
             for (int k = 0; k < NM; ++k) {
-                hi[k] = fmaf(wh, part[k], hi[k]);
+                hi[k] = vfma(V(wh), part[k], hi[k]);
                 part[k] = 0.f;
             }
             return;
-        }
+        } else {
 #pragma unroll
-        for (int k = 0; k < NM; ++k) {
-            if (k >= 2 && k < 2 + D) {
-                // _rn intrinsics: never contracted into FMAs, which would break the
-                // error-free transformations
-                const float p = __fmul_rn(wh, part[k]);
-                const float pe = fmaf(wh, part[k], -p);
-                const float sum = __fadd_rn(hi[k], p);
-                const float bv = __fsub_rn(sum, hi[k]);
-                const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(sum, bv)), __fsub_rn(p, bv));
-                hi[k] = sum;
-                lo[k] = fmaf(wl, part[k], lo[k] + (pe + e));
-            } else {
-                hi[k] = fmaf(wh, part[k], hi[k]);
-                lo[k] = fmaf(wl, part[k], lo[k]);
+            for (int k = 0; k < NM; ++k) {
+                if (k >= 2 && k < 2 + D) {
+                    // _rn intrinsics: never contracted into FMAs, which would break the
+                    // error-free transformations
+                    const float p = __fmul_rn(wh, part[k]);
+                    const float pe = fmaf(wh, part[k], -p);
+                    const float sum = __fadd_rn(hi[k], p);
+                    const float bv = __fsub_rn(sum, hi[k]);
+                    const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(sum, bv)), __fsub_rn(p, bv));
+                    hi[k] = sum;
+                    lo[k] = fmaf(wl, part[k], lo[k] + (pe + e));
+                } else {
+                    hi[k] = fmaf(wh, part[k], hi[k]);
+                    lo[k] = fmaf(wl, part[k], lo[k]);
+                }
+                part[k] = 0.f;
             }
-            part[k] = 0.f;
         }
     };
     fold(0);
@@ -296,9 +336,9 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
         constexpr int sh = Lattice<LAT>::T.shell[I];
-        const float sa = pop.template sv<I>(), sb = pop.template sv<I + 1>();
-        const float ev = sa + sb;
-        const float od = sa - sb;
+        const V sa = pop.template sv<I>(), sb = pop.template sv<I + 1>();
+        const V ev = sa + sb;
+        const V od = sa - sb;
         part[0] += ev;
         part[1] += pop.template tv<I>() + pop.template tv<I + 1>();
         int k = 2;
@@ -307,7 +347,7 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
             constexpr int ca = cv<LAT, I, a>();
             if constexpr (ca == 1) part[2 + a] += od;
             else if constexpr (ca == -1) part[2 + a] -= od;
-            else if constexpr (ca != 0) part[2 + a] = fmaf((float)ca, od, part[2 + a]);
+            else if constexpr (ca != 0) part[2 + a] = vfma(V((float)ca), od, part[2 + a]);
         });
         k = 2 + D;
         static_for<0, D>([&](auto AA) {
@@ -318,14 +358,14 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
                 constexpr int cab = cv<LAT, I, a>() * cv<LAT, I, b>();
                 if constexpr (cab == 1) part[idx] += ev;
                 else if constexpr (cab == -1) part[idx] -= ev;
-                else if constexpr (cab != 0) part[idx] = fmaf((float)cab, ev, part[idx]);
+                else if constexpr (cab != 0) part[idx] = vfma(V((float)cab), ev, part[idx]);
             });
         });
         (void)k;
         constexpr bool last = (I + 2 >= Q) || (Lattice<LAT>::T.shell[I + 2] != sh);
         if constexpr (last) fold(sh);
     });
-    float tot[NM];
+    V tot[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) tot[k] = hi[k] + lo[k];
     m.drho = tot[0];
@@ -336,7 +376,7 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) {
-            const float v = tot[2 + D + a * D - a * (a - 1) / 2 + (b - a)];
+            const V v = tot[2 + D + a * D - a * (a - 1) / 2 + (b - a)];
             m.M[a][b] = v;
             m.M[b][a] = v;
         }
@@ -344,20 +384,20 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
 
 // Macroscopic state from raw moments, rho-weighted: P = r^2 M - drho delta =
 // rho (sigma - delta) + rho u u, rho sdev = rho (sigma - delta), rho theta = rho (T - 1).
-template <int D> struct CellState {
-    float drho, rho, inv_rho;
-    float J[D];           // rho v
-    float v[D];           // lattice-unit velocity J / rho
-    float u[D];           // r v
-    float ruu[D][D];      // rho u u
-    float rsdev[D][D];    // rho (sigma - delta)
-    float rth_tr, rth_int, rth_eq, rth_rel;
-    float th_eq;          // T_eq - 1
+template <int D, class V = float> struct CellState {
+    V drho, rho, inv_rho;
+    V J[D];               // rho v
+    V v[D];               // lattice-unit velocity J / rho
+    V u[D];               // r v
+    V ruu[D][D];          // rho u u
+    V rsdev[D][D];        // rho (sigma - delta)
+    V rth_tr, rth_int, rth_eq, rth_rel;
+    V th_eq;              // T_eq - 1
 };
 
-template <int LAT>
-__device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMoments<Lattice<LAT>::D> &m,
-                                           CellState<Lattice<LAT>::D> &c)
+template <int LAT, class V>
+__device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMoments<Lattice<LAT>::D, V> &m,
+                                           CellState<Lattice<LAT>::D, V> &c)
 {
     constexpr int D = Lattice<LAT>::D;
     c.drho = m.drho;
@@ -369,15 +409,15 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
         c.v[a] = m.J[a] * c.inv_rho;
         c.u[a] = kp.r * c.v[a];
     }
-    float tr = 0.f;
+    V tr = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) {
             // r^2 M in hi + lo: the temperature sees the r^2 the energy sums use
-            const float R2M = fmaf(kp.R2_hi, m.M[a][b], kp.R2_lo * m.M[a][b]);
-            const float ruu = kp.R2_hi * (c.J[a] * c.v[b]);
-            const float v = (R2M - (a == b ? m.drho : 0.f)) - ruu;
+            const V R2M = vfma(kp.R2_hi, m.M[a][b], kp.R2_lo * m.M[a][b]);
+            const V ruu = kp.R2_hi * (c.J[a] * c.v[b]);
+            const V v = (R2M - (a == b ? m.drho : V(0.f))) - ruu;
             c.ruu[a][b] = c.ruu[b][a] = ruu;
             c.rsdev[a][b] = c.rsdev[b][a] = v;
             if (a == b) tr += v;
@@ -388,7 +428,7 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
         c.rth_eq = (D * c.rth_tr + kp.Nf * c.rth_int) / (D + kp.Nf);
         // T_rel = T_int + kappa (T_eq - T_int): equal to T_int at equilibrium whatever the
         // rounding of kappa
-        c.rth_rel = fmaf(kp.kappa, c.rth_eq - c.rth_int, c.rth_int);
+        c.rth_rel = vfma(kp.kappa, c.rth_eq - c.rth_int, c.rth_int);
     } else {
         c.rth_int = 0.f;
         c.rth_eq = c.rth_tr;
@@ -401,9 +441,9 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
 // the same tensor as (1-kappa)[(1-nu) T_tr delta + nu sigma] + kappa T_eq delta - delta written so
 // that its trace, D theta_tr + kappa D (theta_eq - theta_tr), does not depend on rounded
 // complements of kappa (energy closes exactly in the collision).
-template <int LAT>
-__device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState<Lattice<LAT>::D> &c,
-                                         EqState<Lattice<LAT>::D> &e)
+template <int LAT, class V>
+__device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState<Lattice<LAT>::D, V> &c,
+                                         EqState<Lattice<LAT>::D, V> &e)
 {
     constexpr int D = Lattice<LAT>::D;
     e.drho = c.drho;
@@ -411,14 +451,14 @@ __device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState
     e.inv_rho = c.inv_rho;
     e.rth_rel = c.rth_rel;
     e.th_rel = c.rth_rel * c.inv_rho;
-    const float iso = fmaf(kp.kappa, c.rth_eq - c.rth_tr, c.rth_tr);
+    const V iso = vfma(kp.kappa, c.rth_eq - c.rth_tr, c.rth_tr);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         e.J[a] = c.J[a];
         e.u[a] = c.u[a];
 #pragma unroll
         for (int b = 0; b < D; ++b) {
-            const float rA = kp.a_sig * (c.rsdev[a][b] - (a == b ? c.rth_tr : 0.f)) + (a == b ? iso : 0.f);
+            const V rA = kp.a_sig * (c.rsdev[a][b] - (a == b ? c.rth_tr : V(0.f))) + (a == b ? iso : V(0.f));
             e.X[a][b] = rA + c.ruu[a][b];
             e.A[a][b] = rA * c.inv_rho;
         }
@@ -451,14 +491,16 @@ __device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], f
 
 // Scaled equilibrium deviations at velocity I given Pq = rho q(c_I):
 //   G~_I / w_I = drho + Pq,   H~_I / w_I = (N_f/2)(drho + rho th_rel) + (N_f/2)(1 + th_rel) Pq
-struct EqScal {
-    float drho, hb, hr;
-    float om1, wdrho, whb, whr; // 1 - omega and omega-scaled terms (16-bit storage relaxation)
+template <class V = float> struct EqScalT {
+    V drho, hb, hr;
+    float om1;            // 1 - omega
+    V wdrho, whb, whr;    // omega-scaled terms (16-bit storage relaxation)
 };
+using EqScal = EqScalT<float>;
 
-template <int D> __device__ __forceinline__ EqScal eq_scalars(const EqState<D> &e, float halfNf)
+template <int D, class V> __device__ __forceinline__ EqScalT<V> eq_scalars(const EqState<D, V> &e, float halfNf)
 {
-    EqScal z;
+    EqScalT<V> z;
     z.drho = e.drho;
     z.hb = halfNf * (e.drho + e.rth_rel);
     z.hr = halfNf * (1.f + e.th_rel);

@@ -80,8 +80,10 @@ template <int ST> struct TileGeom {
 template <int LAT, int ST> struct SmemPop {
     using G = TileGeom<ST>;
     using S = Storage<ST>;
+    using V = float;
     static constexpr int Q = Lattice<LAT>::Q;
     const typename S::T *base; // stage + H + tx
+    __device__ __forceinline__ void refresh() const {}
     template <int I> __device__ __forceinline__ float sv() const
     {
         constexpr int off = I * G::L - cv<LAT, I, 0>();

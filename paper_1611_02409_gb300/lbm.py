@@ -37,6 +37,7 @@ LBM_WALLS = 1
 LBM_KERNEL_AUTO = 0
 LBM_KERNEL_DIRECT = 1
 LBM_KERNEL_STAGED = 2
+LBM_KERNEL_PAIRED = 3
 LBM_MEM_DEVICE = 0
 LBM_MEM_HOST = 1
 
@@ -112,6 +113,7 @@ def lib():
             L.lbm_batch_init_fields.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
             L.lbm_batch_run.argtypes = [vp, C.c_int, C.c_double, C.c_int, ip]
             L.lbm_batch_status.argtypes = [vp, ip, dp, ip]
+            L.lbm_batch_activate.argtypes = [vp, C.c_int]
             L.lbm_batch_moments.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
             L.lbm_batch_autotune.argtypes = [vp, C.c_int, ip]
             L.lbm_mlp_create.argtypes = [C.c_int, ip, C.c_int, vp, C.POINTER(vp)]
@@ -364,6 +366,10 @@ def lbm_batch_status(b, n):
     return steps, res, act
 
 
+def lbm_batch_activate(b, i=-1):
+    return _check(lib().lbm_batch_activate(b, int(i)))
+
+
 def lbm_batch_moments(b, i, rho=None, u=None, T=None, Pi=None, q=None):
     xs = [x for x in (rho, u, T, Pi, q) if x is not None]
     mem = _mem_of(*xs) if xs else LBM_MEM_DEVICE
@@ -408,6 +414,9 @@ class Batch:
 
     def autotune(self, steps=20):
         return lbm_batch_autotune(self.b, steps)
+
+    def activate(self, i=-1):
+        return lbm_batch_activate(self.b, i)
 
     def close(self):
         if getattr(self, "b", None):

@@ -81,3 +81,78 @@ def run_sweep(lbm, cases, max_steps=20000, tol=1e-8, check_every=100, autotune=T
     bt.close()
     status = dict(batch_steps=done, steps=steps, residual=res, active=act, tile=tile)
     return status, np.array(prof), np.array(xin), np.array(conv), secs
+
+
+COUETTE_PR = (0.5, 0.71, 1.0, 2.0)
+COUETTE_GAMMA = (1.3, 1.4, 1.67)
+
+
+def couette_grid(H=256, U=0.05, T_bottom=1.0, T_top=1.02, tau=0.528655, nx=4, kappa=0.2):
+    """The Pr x gamma grid of thermal Couette channels nx x H: bottom wall at rest at
+    T_bottom, top wall moving at U (paper units, sqrt(theta_0) = 1) at T_top; tau gives
+    nu = 0.02 lattice units on D2Q37."""
+    return [dict(kind="channel", inputs=np.array([Pr, g, U, tau, T_top - T_bottom]),
+                 params=dict(nx=nx, ny=H, Pr=Pr, gamma=g, kappa=kappa, tau=tau, bc_y=1,
+                             wall_u=[[0, 0, 0], [U, 0, 0]], wall_T=[T_bottom, T_top]))
+            for Pr in COUETTE_PR for g in COUETTE_GAMMA]
+
+
+def run_couette(lbm, cases, tol=1e-8, settle_steps=0, check_every=1000, max_steps=5_000_000):
+    """All cases in one batch from rest: steps to residual `tol`, then (if settle_steps)
+    every case continues `settle_steps` more steps.  Returns per-case steps to tol,
+    x-averaged u_x and T profiles at tol and after settling, and seconds."""
+    import time
+    bt = lbm.Batch([c["params"] for c in cases])
+    for i, c in enumerate(cases):
+        bt.init(i, *initial_fields(c))
+    t0 = time.perf_counter()
+    bt.run(max_steps, tol=tol, check_every=check_every)
+    secs = time.perf_counter() - t0
+    steps, res, act = bt.status()
+    prof = lambda m: np.stack([m["u"][0].mean(1), m["T"].mean(1)])
+    at_tol = [prof(bt.moments(i)) for i in range(len(cases))]
+    out = dict(steps_to_tol=steps.copy(), converged=act == 0, residual=res.copy(), seconds_to_tol=secs,
+               profiles_at_tol=np.array(at_tol))
+    if settle_steps:
+        bt.activate()
+        t0 = time.perf_counter()
+        bt.run(settle_steps, tol=0.0, check_every=check_every)
+        out["seconds_settle"] = time.perf_counter() - t0
+        out["steps_total"] = bt.status()[0]
+        out["profiles_settled"] = np.array([prof(bt.moments(i)) for i in range(len(cases))])
+    bt.close()
+    return out
+
+
+def main():
+    """The full sweep: 256 squares + 256 channels, one batch, residual 1e-8 or 20k steps."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--max-steps", type=int, default=20000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    from . import build, lbm
+    build.build()
+    cases = draw_instances()
+    ncomp = np.array([c["params"]["nx"] * (c["params"]["ny"] - (2 if c["kind"] == "channel" else 0))
+                      for c in cases], dtype=np.float64)
+    status, prof, xin, conv, secs = run_sweep(lbm, cases, max_steps=a.max_steps, tol=a.tol,
+                                              check_every=a.check_every, autotune=True)
+    updates = float(np.sum(ncomp * status["steps"]))
+    kinds = np.array([c["kind"] for c in cases])
+    res = dict(instances=len(cases), cells_total=float(ncomp.sum()), batch_steps=int(status["batch_steps"]),
+               tile=int(status["tile"]), seconds=secs, cell_updates=updates, mlups=updates / secs / 1e6,
+               converged_channels=int(conv.sum()), channels=int((kinds == "channel").sum()),
+               converged_squares=int(((status["active"] == 0) & (kinds == "square")).sum()),
+               channel_heights_converged=[int(c["params"]["ny"]) for c, k in zip(cases, status["active"])
+                                          if c["kind"] == "channel" and k == 0])
+    print(json.dumps(res))
+    if a.out:
+        np.savez_compressed(a.out, X=xin, Y=prof, converged=conv)
+
+
+if __name__ == "__main__":
+    main()

@@ -54,15 +54,19 @@ def test_surrogate_warm_start_saves_steps(L):
     test = S.draw_channels(6, seed=77, H=17)
     pred = sur.predict(np.array([c["inputs"] for c in test]))
     tol = 1e-9
-    rest, _ = S.run_channels(L, test, lambda i, bt: bt.init(i, *sweep.initial_fields(test[i])), tol, 400000, 100)
-    warm, _ = S.run_channels(L, test, lambda i, bt: bt.init_neq(i, *S.warm_fields(test[i], pred[i])), tol,
-                             400000, 100)
+    rest, _, br = S.run_channels(L, test, lambda i, bt: bt.init(i, *sweep.initial_fields(test[i])), tol, 400000,
+                                 100)
+    warm, _, bw = S.run_channels(L, test, lambda i, bt: bt.init_neq(i, *S.warm_fields(test[i], pred[i])), tol,
+                                 400000, 100)
     assert rest["converged"].all() and warm["converged"].all()
     assert np.median(warm["steps"]) < 0.8 * np.median(rest["steps"]), (warm["steps"], rest["steps"])
-    n_long = int(3 * max(rest["steps"]))
-    _, fr = S.run_channels(L, test, lambda i, bt: bt.init(i, *sweep.initial_fields(test[i])), 0.0, n_long, 100)
-    _, fw = S.run_channels(L, test, lambda i, bt: bt.init_neq(i, *S.warm_fields(test[i], pred[i])), 0.0,
-                           n_long, 100)
+    # continue both batches (lbm_batch_activate) well past convergence: tol 0 never stops
+    n_long = int(2 * max(rest["steps"]))
+    r2, fr = S.continue_channels(br, len(test), 0.0, n_long, 100)
+    w2, fw = S.continue_channels(bw, len(test), 0.0, n_long, 100)
+    br.close()
+    bw.close()
+    assert (r2["steps"] - rest["steps"] >= n_long).all() and (w2["steps"] - warm["steps"] >= n_long).all()
     for i in range(len(test)):
         for k in ("u", "T"):
             assert np.linalg.norm(fw[i][k] - fr[i][k]) <= 1e-5 * np.linalg.norm(fr[i][k]), (i, k)
