@@ -108,6 +108,8 @@ def hermite_coeff(n: int, u, Lam) -> np.ndarray:
     u = _f64(u)
     Lam = _f64(Lam)
     D = u.size
+    if Lam.size != D * D:
+        raise ValueError(f"Lambda must be {D}x{D}")
     out = np.zeros(D ** n)
     if lib().orc_hermite_coeff(n, D, _dp(u), _dp(Lam.reshape(-1)), _dp(out)):
         raise ValueError("bad order")
@@ -119,6 +121,8 @@ def equilibrium(which: int, rho: float, u, Lam, order: int = 4) -> np.ndarray:
     D, _, c, _ = lattice(which)
     u = _f64(u)
     Lam = _f64(Lam).reshape(-1)
+    if u.shape != (D,) or Lam.shape != (D * D,):
+        raise ValueError(f"u needs {D} components and Lambda {D}x{D}")
     G = np.zeros(len(c))
     if lib().orc_equilibrium(which, order, rho, _dp(u), _dp(Lam), _dp(G)):
         raise ValueError("bad args")

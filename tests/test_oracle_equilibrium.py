@@ -89,7 +89,7 @@ def test_equilibrium_order4_truncation_differs_from_order6():
     assert np.abs(G4 - G6).max() > 1e-6
 
 
-def _perturbed_state(sim, rho=1.05, u=(0.05, -0.03), T=1.02, amp=2e-3):
+def _perturbed_state(sim, rho=1.05, u=(0.05, -0.03, 0.02), T=1.02, amp=2e-3):
     D = sim.D
     u = np.array(u[:D], float)
     G = O.equilibrium(O.D2Q37 if D == 2 else O.D3Q103, rho, u, T * np.eye(D))
