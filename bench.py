@@ -280,29 +280,39 @@ def bench_batch(torch, lbm, steps):
 def bench_couette(lbm):
     """The Pr x gamma thermal Couette grid (4 x 256, U = 0.05, T 1.0 / 1.02), one batch:
     steps to residual 1e-8, then nine decay times of the slowest thermal mode more; u and
-    T profiles against the analytic steady solution (Eq. CouetteDi3, unequal walls)."""
+    T profiles against the analytic steady solution (Eq. CouetteDi3, unequal walls).  The
+    same grid at 4 x 64, where FP32 resolves the viscous heating, gives the fitted heating
+    curvature against the analytic one."""
     from paper_1611_02409_gb300 import sweep
-    cases = sweep.couette_grid()
-    H = cases[0]["params"]["ny"]
     nu = 0.02
-    settle = int(9 * (H - 1) ** 2 / (np.pi ** 2 * nu / max(sweep.COUETTE_PR)))
-    out = sweep.run_couette(lbm, cases, tol=1e-8, settle_steps=settle, check_every=1000)
-    eta = np.arange(H) / (H - 1)
-    rows = []
-    for i, c in enumerate(cases):
-        Pr, gamma, U, _, dT = c["inputs"]
-        heat = Pr * U ** 2 / (2 + 2.0 / (gamma - 1.0) - 2.0 + 2)
-        T_an = 1.0 + dT * eta + heat * eta * (1 - eta)
-        err = lambda p: (float(np.abs(p[0] - U * eta).max() / U), float(np.abs(p[1] - T_an).max() / (heat / 4)))
-        eu8, eT8 = err(out["profiles_at_tol"][i])
-        eu, eT = err(out["profiles_settled"][i])
-        rows.append(dict(Pr=float(Pr), gamma=float(gamma), steps_to_1e8=int(out["steps_to_tol"][i]),
-                         u_err_at_1e8=eu8, T_err_at_1e8=eT8, u_err=eu, T_err=eT))
-    return {"workload": "thermal Couette 4x256, top wall U=0.05 T=1.02, bottom T=1.0, tau=0.528655, "
-                        "Pr x gamma = {0.5,0.71,1,2} x {1.3,1.4,1.67}, FP32, one batch",
-            "settle_steps": settle, "seconds_to_1e8": out["seconds_to_tol"], "seconds_settle": out["seconds_settle"],
-            "errors": "u: max|u - U eta| / U; T: max|T - T_analytic| / (peak viscous heating Pr U^2 / (4 (D+N_f+2)))",
-            "max_u_err": max(r["u_err"] for r in rows), "max_T_err": max(r["T_err"] for r in rows), "cases": rows}
+    res = {"workload": "thermal Couette 4xH, top wall U=0.05 T=1.02, bottom T=1.0, tau=0.528655, "
+                       "Pr x gamma = {0.5,0.71,1,2} x {1.3,1.4,1.67}, FP32, one batch",
+           "errors": "u: max|u - U eta| / U; T: max|T - T_analytic| / (T_top - T_bottom); "
+                     "curvature: fitted viscous-heating coefficient / Pr U^2 / (D+N_f+2)"}
+    for H in (256, 64):
+        cases = sweep.couette_grid(H=H)
+        settle = int(9 * (H - 1) ** 2 / (np.pi ** 2 * nu / max(sweep.COUETTE_PR)))
+        out = sweep.run_couette(lbm, cases, tol=1e-8, settle_steps=settle, check_every=1000)
+        eta = np.arange(H) / (H - 1)
+        A = np.stack([eta * (1 - eta), eta - 0.5, np.ones_like(eta)], 1)
+        rows = []
+        for i, c in enumerate(cases):
+            Pr, gamma, U, _, dT = c["inputs"]
+            heat = Pr * U ** 2 / (2 + 2.0 / (gamma - 1.0) - 2.0 + 2)
+            T_an = 1.0 + dT * eta + heat * eta * (1 - eta)
+            err = lambda p: (float(np.abs(p[0] - U * eta).max() / U), float(np.abs(p[1] - T_an).max() / dT))
+            eu8, eT8 = err(out["profiles_at_tol"][i])
+            eu, eT = err(out["profiles_settled"][i])
+            curv = float(np.linalg.lstsq(A, out["profiles_settled"][i][1] - (1.0 + dT * eta), rcond=None)[0][0] / heat)
+            rows.append(dict(Pr=float(Pr), gamma=float(gamma), steps_to_1e8=int(out["steps_to_tol"][i]),
+                             u_err_at_1e8=eu8, T_err_at_1e8=eT8, u_err=eu, T_err=eT, curvature_ratio=curv))
+        res[f"H{H}"] = {"settle_steps": settle, "seconds_to_1e8": out["seconds_to_tol"],
+                        "seconds_settle": out["seconds_settle"], "all_converged": bool(out["converged"].all()),
+                        "max_u_err": max(r["u_err"] for r in rows), "max_T_err": max(r["T_err"] for r in rows),
+                        "curvature_ratio_range": [min(r["curvature_ratio"] for r in rows),
+                                                  max(r["curvature_ratio"] for r in rows)],
+                        "cases": rows}
+    return res
 
 
 def bench_warm_start(lbm):
@@ -420,7 +430,7 @@ def run_ours(args):
     h2d = 8 * cells * 4
     d2h = 8 * cells * 4
     extra = {}
-    if ws == 1:
+    if ws == 1 and args.extras == "all":
         # the other configurations, measured at one GPU only (they hold no other rank)
         _extra(extra, "accuracy", lambda: accuracy_vs_oracle(lbm))
         _extra(extra, "d3q103_256", lambda: bench_3d(torch, lbm, max(args.steps // 8, 20), args.warmup, peak))
@@ -466,6 +476,8 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--extras", default="all", choices=["all", "none"],
+                    help="none: only the timed 4096^2 runs (for profiler launch lists)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

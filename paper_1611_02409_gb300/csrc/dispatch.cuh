@@ -110,8 +110,17 @@ template <int LAT, int ST> struct Launch {
         }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
         const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
-        if (c.walls)
-            k_stream_collide<LAT, ST, true><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
+        // walls are 2-D only (the create call rejects them for D = 3): no 3-D wall kernels
+        constexpr bool W2 = Lattice<LAT>::D == 2;
+        if (c.kernel == 4) {
+            if (W2 && c.walls)
+                k_stream_collide_2p<LAT, ST, W2><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
+            else
+                k_stream_collide_2p<LAT, ST, false><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
+            return;
+        }
+        if (W2 && c.walls)
+            k_stream_collide<LAT, ST, W2><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
         else
             k_stream_collide<LAT, ST, false><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
     }
@@ -164,13 +173,5 @@ template <int LAT, int ST> Ops make_ops_st()
     return o;
 }
 
-template <int LAT> Ops make_ops(int storage)
-{
-    switch (storage) {
-    case ST_FP16: return make_ops_st<LAT, ST_FP16>();
-    case ST_BF16: return make_ops_st<LAT, ST_BF16>();
-    default: return make_ops_st<LAT, ST_FP32>();
-    }
-}
 
 } // namespace lbm

@@ -101,15 +101,17 @@ __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop 
     typename Storage<ST>::T *cell = dst + o;
     Off so = off;
     if constexpr (std::is_same<Off, TableOff>::value) so.soff = kp.soff;
-    pop.refresh();
-    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], pop.template sv<0>(), pop.template tv<0>());
+    Pop rp = pop;
+    rp.refresh();
+    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], rp.template sv<0>(), rp.template tv<0>());
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
+        rp.template prefetch<decltype(PP)::value>();
         V E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
-        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, pop.template sv<I>(), pop.template tv<I>());
-        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, pop.template sv<I + 1>(),
-                             pop.template tv<I + 1>());
+        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, rp.template sv<I>(), rp.template tv<I>());
+        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, rp.template sv<I + 1>(),
+                             rp.template tv<I + 1>());
     });
 }
 
@@ -136,9 +138,9 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    // a block away from every periodic seam (|c| <= 3) gathers at fixed byte offsets
-    const int xb = blockIdx.x * blockDim.x;
-    bool interior = xb >= 3 && xb + (int)blockDim.x + 3 <= kp.nx;
+    // a cell away from every periodic seam (|c| <= 3) gathers at fixed byte offsets; only
+    // the warps holding the first and last three cells of a row diverge
+    bool interior = x >= 3 && x + 3 < kp.nx;
     if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
     if constexpr (D == 3) interior = interior && z >= 3 && z + 3 < kp.nz;
     typename S::Raw rs[Q], rt[Q];
@@ -176,6 +178,94 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
     collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o);
 }
 
+// Populations read from the source buffer where they are used (two-pass kernel): a cell's
+// wrapped source columns, rows and planes for the displacements -3..3 are tabulated once.
+// Opposite pairs are read in chunks of CH pairs: prefetch<P>() at the first pair of a
+// chunk issues the chunk's 4 CH loads (g and h of both members) into registers before any
+// of them is used, so each warp keeps a chunk of loads in flight; sv<I>() / tv<I>() then
+// return the buffered values (the rest population is read directly).  refresh() makes
+// the buffer address opaque, so the relaxation reads the values again (from L1 / L2)
+// instead of keeping the moment pass's values live across the cell.
+template <int LAT, int ST, int CH> struct GatherPop {
+    using V = float;
+    using S = Storage<ST>;
+    using T = typename S::T;
+    static constexpr int Q = Lattice<LAT>::Q;
+    static constexpr int NP = (Q - 1) / 2;
+    const T *src;
+    long long plane;
+    int col[7], row[7], pln[7];   // element offsets within a population plane
+    mutable typename S::Raw bs[2 * CH], bt[2 * CH];
+    template <int I> __device__ __forceinline__ int at() const
+    {
+        return pln[cv<LAT, I, 2>() + 3] + row[cv<LAT, I, 1>() + 3] + col[cv<LAT, I, 0>() + 3];
+    }
+    template <int P> __device__ __forceinline__ void prefetch() const
+    {
+        if constexpr (P % CH == 0) {
+            static_for<0, CH>([&](auto KK) {
+                constexpr int k = decltype(KK)::value;
+                constexpr int I = 1 + 2 * (P + k);
+                if constexpr (P + k < NP) {
+                    bs[2 * k] = S::raw(src + I * plane + at<I>());
+                    bs[2 * k + 1] = S::raw(src + (I + 1) * plane + at<I + 1>());
+                    bt[2 * k] = S::raw(src + (Q + I) * plane + at<I>());
+                    bt[2 * k + 1] = S::raw(src + (Q + I + 1) * plane + at<I + 1>());
+                }
+            });
+            asm volatile("" ::: "memory");
+        }
+    }
+    template <int I> __device__ __forceinline__ float sv() const
+    {
+        if constexpr (I == 0) return S::ld(src + at<0>());
+        else return S::cvt(bs[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
+    }
+    template <int I> __device__ __forceinline__ float tv() const
+    {
+        if constexpr (I == 0) return S::ld(src + Q * plane + at<0>());
+        else return S::cvt(bt[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
+    }
+    __device__ __forceinline__ void refresh() { asm volatile("" : "+l"(src)); }
+};
+
+// Pairs per prefetch chunk of the two-pass kernel: D2Q37's 18 pairs in two chunks,
+// D3Q103's 51 in three.
+template <int LAT> constexpr int twopass_chunk() { return Lattice<LAT>::D == 2 ? 9 : 17; }
+
+// The fused step with the populations read twice: once streamed into the moment sums,
+// once more for the relaxation.  Nothing of the cell stays in registers between the
+// passes, so the kernel fits a lattice whose 2Q values would not (D3Q103, 206 values):
+// more resident warps in exchange for a second, cache-served read.  Every cell takes the
+// same tabulated-offset gather (no seam divergence).
+template <int LAT> constexpr int twopass_min_blocks() { return Lattice<LAT>::D == 2 ? 4 : 2; }
+
+template <int LAT, int ST, bool WALLS>
+__global__ void __launch_bounds__(128, twopass_min_blocks<LAT>()) k_stream_collide_2p(
+    const typename Storage<ST>::T *__restrict__ src, typename Storage<ST>::T *__restrict__ dst,
+    const KParams<LAT> kp, int small_x, int small_y, int small_z)
+{
+    constexpr int D = Lattice<LAT>::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= kp.nx) return;
+    const int y = blockIdx.y + kp.y0;
+    const int z = blockIdx.z;
+    GatherPop<LAT, ST, twopass_chunk<LAT>()> pop;
+    pop.src = src;
+    pop.plane = kp.plane;
+    static_for<0, 7>([&](auto KK) {
+        constexpr int C = decltype(KK)::value - 3;
+        pop.col[KK] = wrap_sub<C>(x, kp.nx, small_x);
+        int ys;
+        if constexpr (WALLS) ys = y - C + kp.gh;
+        else ys = wrap_sub<C>(y, kp.ny, small_y);
+        pop.row[KK] = ys * kp.nx;
+        if constexpr (D == 3) pop.pln[KK] = wrap_sub<C>(z, kp.nz, small_z) * kp.nys * kp.nx;
+        else pop.pln[KK] = 0;
+    });
+    collide_store<LAT, ST>(kp, pop, dst, cell_index<LAT>(kp, x, y + kp.gh, z));
+}
+
 // Two neighbouring cells' stored 16-bit values, one 32-bit word per population (low
 // half: the even cell).  Values are converted to FP32 pairs where they are used; refresh()
 // makes the words opaque between the moment sums and the relaxation, so the converted
@@ -185,7 +275,8 @@ template <int ST, int Q> struct RawPop2 {
     uint32_t *s, *t;
     template <int I> __device__ __forceinline__ f2 sv() const { return Storage<ST>::cvt2(s[I]); }
     template <int I> __device__ __forceinline__ f2 tv() const { return Storage<ST>::cvt2(t[I]); }
-    __device__ __forceinline__ void refresh() const
+    template <int P> __device__ __forceinline__ void prefetch() const {}
+    __device__ __forceinline__ void refresh()
     {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -227,18 +318,32 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
     const int xb = 2 * blockIdx.x * blockDim.x;
     bool interior = xb >= 4 && xb + 2 * (int)blockDim.x + 4 <= kp.nx;
     if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
-    uint32_t rs[Q], rt[Q];
+    // every load of the cell is issued before any word is combined (the byte permutes
+    // and shifts wait for their loads): raw words first, then a compiler barrier
+    uint32_t rs[Q], rt[Q], xs[Q], xt[Q];
     if (interior) {
         const char *base = reinterpret_cast<const char *>(src + o);
         static_for<0, Q>([&](auto II) {
             constexpr int I = decltype(II)::value;
             constexpr int cx = cv<LAT, I, 0>();
+            const char *ps = base + kp.goff[I], *pt = base + kp.goff[Q + I];
             if constexpr (cx % 2 == 0) {
-                rs[I] = __ldg(reinterpret_cast<const unsigned int *>(base + kp.goff[I]));
-                rt[I] = __ldg(reinterpret_cast<const unsigned int *>(base + kp.goff[Q + I]));
+                rs[I] = __ldg(reinterpret_cast<const unsigned int *>(ps));
+                rt[I] = __ldg(reinterpret_cast<const unsigned int *>(pt));
             } else {
-                rs[I] = ld_pair_odd(base + kp.goff[I]);
-                rt[I] = ld_pair_odd(base + kp.goff[Q + I]);
+                // the aligned words before and after the odd element
+                rs[I] = __ldg(reinterpret_cast<const unsigned int *>(ps - 2));
+                xs[I] = __ldg(reinterpret_cast<const unsigned int *>(ps + 2));
+                rt[I] = __ldg(reinterpret_cast<const unsigned int *>(pt - 2));
+                xt[I] = __ldg(reinterpret_cast<const unsigned int *>(pt + 2));
+            }
+        });
+        asm volatile("" ::: "memory");
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            if constexpr (cv<LAT, I, 0>() % 2 != 0) {
+                rs[I] = __byte_perm(rs[I], xs[I], 0x5432);
+                rt[I] = __byte_perm(rt[I], xt[I], 0x5432);
             }
         });
     } else {
@@ -255,11 +360,18 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
             else ys = wrap_sub<cy>(y, kp.ny, small_y);
             const long long row = (long long)ys * kp.nx;
             const long long ps = (long long)I * kp.plane + row, pt = (long long)(Q + I) * kp.plane + row;
-            rs[I] = (uint32_t)__ldg(sp + ps + x0) | ((uint32_t)__ldg(sp + ps + x1) << 16);
-            rt[I] = (uint32_t)__ldg(sp + pt + x0) | ((uint32_t)__ldg(sp + pt + x1) << 16);
+            rs[I] = __ldg(sp + ps + x0);
+            xs[I] = __ldg(sp + ps + x1);
+            rt[I] = __ldg(sp + pt + x0);
+            xt[I] = __ldg(sp + pt + x1);
+        });
+        asm volatile("" ::: "memory");
+        static_for<0, Q>([&](auto II) {
+            constexpr int I = decltype(II)::value;
+            rs[I] |= xs[I] << 16;
+            rt[I] |= xt[I] << 16;
         });
     }
-    asm volatile("" ::: "memory");
     collide_store<LAT, ST>(kp, RawPop2<ST, Q>{rs, rt}, dst, o);
 }
 

@@ -40,6 +40,17 @@ struct lbm_handle {
     std::string err;
 };
 
+// The measured-fastest variant for the configuration (GB300, 4096^2 / 256^3 workloads):
+// paired cells for 16-bit storage on the 2-D lattice (even rows), the two-pass kernel for
+// the 3-D lattice (its 206 values per cell do not fit the register file), else direct.
+static int default_kernel(const lbm_handle *h)
+{
+    if (h->ops.paired_ok(h->ctx)) return LBM_KERNEL_PAIRED;
+    if (h->D == 3) return LBM_KERNEL_TWOPASS;
+    return LBM_KERNEL_DIRECT;
+}
+
+
 namespace {
 
 thread_local std::string g_create_err;
@@ -277,7 +288,7 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
         for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
         c.wall_T[b] = p.wall_T[b];
     }
-    h->ops = D == 2 ? lbm::ops_d2q37(p.storage) : lbm::ops_d3q103(p.storage);
+    h->ops = lbm::ops_for(D, p.storage);
     h->elem = p.storage == LBM_FP32 ? 4 : 2;
     h->buf_elems = (size_t)2 * h->Q * (size_t)c.plane;
     for (int k = 0; k < 2; ++k) {
@@ -294,7 +305,7 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
-    h->ctx.kernel = LBM_KERNEL_DIRECT;
+    h->ctx.kernel = default_kernel(h);
     cudaError_t e = cudaMalloc(&h->d_partials, sizeof(double) * lbm::kDiagNV * (h->diag_blocks + 1));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
@@ -512,12 +523,12 @@ int lbm_diagnostics(lbm_handle *h, double *out)
 int lbm_set_kernel(lbm_handle *h, int variant)
 {
     if (!h) return LBM_ERR_ARG;
-    if (variant == LBM_KERNEL_AUTO) variant = LBM_KERNEL_DIRECT;
+    if (variant == LBM_KERNEL_AUTO) variant = default_kernel(h);
     if (variant == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx))
         return set_err(h, LBM_ERR_ARG, "staged kernel needs D = 2 and nx a multiple of 128");
     if (variant == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx))
         return set_err(h, LBM_ERR_ARG, "paired kernel needs D = 2, 16-bit storage and nx even");
-    if (variant < LBM_KERNEL_DIRECT || variant > LBM_KERNEL_PAIRED) return set_err(h, LBM_ERR_ARG, "bad variant");
+    if (variant < LBM_KERNEL_DIRECT || variant > LBM_KERNEL_TWOPASS) return set_err(h, LBM_ERR_ARG, "bad variant");
     h->ctx.kernel = variant;
     return LBM_OK;
 }
@@ -530,7 +541,7 @@ int lbm_autotune(lbm_handle *h, int steps, int *chosen)
     LBM_CK(h, cudaEventCreate(&e1));
     float best = -1.f;
     int best_v = LBM_KERNEL_DIRECT;
-    for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_PAIRED; ++v) {
+    for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_TWOPASS; ++v) {
         if (v == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx)) continue;
         if (v == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx)) continue;
         h->ctx.kernel = v;

@@ -32,8 +32,19 @@ struct Ops {
     bool (*paired_ok)(const Ctx &);
 };
 
-Ops ops_d2q37(int storage);
-Ops ops_d3q103(int storage);
+Ops ops_d2q37_fp32();
+Ops ops_d2q37_fp16();
+Ops ops_d2q37_bf16();
+Ops ops_d3q103_fp32();
+Ops ops_d3q103_fp16();
+Ops ops_d3q103_bf16();
+
+// The launch table of a lattice (2 = D2Q37, 3 = D3Q103 by dimension) and storage form.
+inline Ops ops_for(int D, int storage)
+{
+    if (D == 2) return storage == 1 ? ops_d2q37_fp16() : storage == 2 ? ops_d2q37_bf16() : ops_d2q37_fp32();
+    return storage == 1 ? ops_d3q103_fp16() : storage == 2 ? ops_d3q103_bf16() : ops_d3q103_fp32();
+}
 void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);
 
 }  // namespace lbm

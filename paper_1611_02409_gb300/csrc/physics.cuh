@@ -266,11 +266,14 @@ template <int D, class V = float> struct RawMoments {
 // Population accessors: pop.template sv<I>() / tv<I>() return the scaled deviations s_I,
 // t_I of one cell (from registers, or from a shared-memory tile) as V; refresh() is
 // called between the moment sums and the relaxation (a no-op unless the accessor
-// re-converts stored values there instead of keeping them live).
+// re-converts or re-reads stored values there instead of keeping them live), and
+// prefetch<P>() before the opposite pair P is used (a no-op unless the accessor reads
+// memory in chunks of pairs).
 struct ArrayPop {
     using V = float;
     const float *s, *t;
-    __device__ __forceinline__ void refresh() const {}
+    __device__ __forceinline__ void refresh() {}
+    template <int P> __device__ __forceinline__ void prefetch() const {}
     template <int I> __device__ __forceinline__ float sv() const { return s[I]; }
     template <int I> __device__ __forceinline__ float tv() const { return t[I]; }
 };
@@ -336,6 +339,7 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
         constexpr int sh = Lattice<LAT>::T.shell[I];
+        pop.template prefetch<decltype(PP)::value>();
         const V sa = pop.template sv<I>(), sb = pop.template sv<I + 1>();
         const V ev = sa + sb;
         const V od = sa - sb;

@@ -83,7 +83,8 @@ template <int LAT, int ST> struct SmemPop {
     using V = float;
     static constexpr int Q = Lattice<LAT>::Q;
     const typename S::T *base; // stage + H + tx
-    __device__ __forceinline__ void refresh() const {}
+    __device__ __forceinline__ void refresh() {}
+    template <int P> __device__ __forceinline__ void prefetch() const {}
     template <int I> __device__ __forceinline__ float sv() const
     {
         constexpr int off = I * G::L - cv<LAT, I, 0>();

@@ -38,6 +38,7 @@ LBM_KERNEL_AUTO = 0
 LBM_KERNEL_DIRECT = 1
 LBM_KERNEL_STAGED = 2
 LBM_KERNEL_PAIRED = 3
+LBM_KERNEL_TWOPASS = 4
 LBM_MEM_DEVICE = 0
 LBM_MEM_HOST = 1
 

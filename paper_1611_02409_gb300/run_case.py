@@ -20,7 +20,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "staged"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "staged", "paired", "twopass"])
     a = ap.parse_args()
     import torch
 
@@ -28,7 +28,7 @@ def main():
     build.build()
     n = a.grid
     params = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655, storage=a.storage,
-                  kernel={"auto": 0, "direct": 1, "staged": 2}[a.kernel])
+                  kernel={"auto": 0, "direct": 1, "staged": 2, "paired": 3, "twopass": 4}[a.kernel])
     if a.lattice == "d2q37":
         sim = lbm.Simulation(lattice=lbm.LBM_D2Q37, nx=n, ny=n, **params)
         fields = inputs.taylor_green_2d(n)

@@ -332,7 +332,7 @@ def test_staged_path_walls(L):
 def test_autotune_selects_a_variant_and_resets(L):
     sim = L.Simulation(nx=256, ny=64, **CFG0)
     v = L.lbm_autotune(sim.h, 5)
-    assert v in (1, 2)
+    assert v in (1, 2, 4)
     m = sim.moments()
     assert np.abs(m["rho"] - 1).max() == 0 and np.abs(m["u"]).max() == 0
     assert sim.diagnostics()["steps"] == 0

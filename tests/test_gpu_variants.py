@@ -1,0 +1,144 @@
+"""Kernel variants against the FP64 oracle, cell by cell: the paired-cell kernel (two
+neighbouring cells per thread in packed FP32 pairs, FP16/BF16 storage, 2-D) and the
+two-pass kernel (populations read once for the moments and again for the relaxation),
+on ragged grids that exercise their seam, wrap and wall paths, plus their admissibility.
+
+Tolerances as in the direct kernel's tests: FP32 storage 2e-6 on the scaled deviations
+after 1 and 9 steps; 16-bit storage a few storage roundings of |s| <~ 0.3 per step
+(2^-11 FP16, 2^-8 BF16)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_02409_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CFG0 = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
+WALLS = dict(bc_y=1, wall_u=[[0, 0, 0], [0.1, 0, 0]], wall_T=[1.0, 1.02])
+TOL = {"fp32": 2e-6, "fp16": 2e-3, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1611_02409_gb300 import build
+    build.build()
+    from paper_1611_02409_gb300 import lbm
+    return lbm
+
+
+def elementwise(L, shape, kernel, storage, steps=(1, 9), walls=False, seed=0, lattice=1, **kw):
+    fields = inputs.random_fields(shape, seed=seed, drho=0.01, du=0.02, dT=0.02)
+    nz, ny, nx = shape if len(shape) == 3 else (1,) + shape
+    p = dict(CFG0, **(WALLS if walls else {}), **kw)
+    sim = L.Simulation(lattice=lattice, nx=nx, ny=ny, nz=nz, storage=storage, kernel=kernel, **p)
+    sim.init(*fields)
+    op = {k: v for k, v in p.items() if k != "bc_y"}
+    o = O.Sim(O.D2Q37 if lattice == 1 else O.D3Q103, nx=nx, ny=ny, nz=nz, walls=walls, **op)
+    o.init(*fields)
+    idx = [next(j for j in range(len(o.c)) if tuple(o.c[j]) == tuple(v)) for v in sim.c]
+    w = sim.w[(slice(None),) + (None,) * len(shape)]
+    errs = []
+    for n in steps:
+        sim.step(n)
+        o.step(n)
+        gg, hg = sim.populations()
+        go, ho = o.populations()
+        errs.append((np.abs((gg - go[idx]) / w).max(), np.abs((hg - ho[idx]) / w).max()))
+    sim.close()
+    return errs
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("nx,ny", [(1024, 12), (130, 9), (2, 7), (10, 4)])
+def test_paired_elementwise(L, storage, nx, ny):
+    # 1024: interior blocks and both seams; 130: one partial block (65 pairs) across the
+    # seam; 2 and 10: rows shorter than the stencil (modulo wrap)
+    for eg, eh in elementwise(L, (ny, nx), L.LBM_KERNEL_PAIRED, storage, seed=nx + ny):
+        assert eg < TOL[storage] and eh < 3 * TOL[storage], (eg, eh)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_paired_walls(L, storage):
+    for eg, eh in elementwise(L, (9, 1040), L.LBM_KERNEL_PAIRED, storage, walls=True, tau=0.8):
+        assert eg < TOL[storage] and eh < 3 * TOL[storage], (eg, eh)
+
+
+def test_paired_and_direct_16bit_against_oracle(L):
+    # the packed and the one-cell kernels round differently (the packed products are not
+    # contracted into FMAs), so each carries its own FP16 storage rounding walk: after
+    # 200 steps of a smooth flow each is within the FP16 bar of the oracle, and they are
+    # within twice that of each other
+    fields = inputs.taylor_green_2d(256, U0=0.02, T_amp=0.01)
+    o = O.Sim(O.D2Q37, nx=256, ny=256, **CFG0)
+    o.init(*fields)
+    o.step(200)
+    mo = o.moments()
+    out = {}
+    for k in (L.LBM_KERNEL_DIRECT, L.LBM_KERNEL_PAIRED):
+        sim = L.Simulation(nx=256, ny=256, storage="fp16", kernel=k, **CFG0)
+        sim.init(*fields)
+        sim.step(200)
+        out[k] = sim.moments()
+        sim.close()
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    for f in ("rho", "u", "T"):
+        a, b = out[L.LBM_KERNEL_DIRECT][f], out[L.LBM_KERNEL_PAIRED][f]
+        assert rel(a, mo[f]) <= 1e-3 and rel(b, mo[f]) <= 1e-3, f
+        assert rel(b, a) <= 2e-3, f
+
+
+def test_paired_admissibility(L):
+    sim = L.Simulation(nx=33, ny=8, storage="fp16", **CFG0)       # odd nx
+    with pytest.raises(RuntimeError):
+        L.lbm_set_kernel(sim.h, L.LBM_KERNEL_PAIRED)
+    sim.close()
+    sim = L.Simulation(nx=32, ny=8, storage="fp32", **CFG0)       # FP32 storage
+    with pytest.raises(RuntimeError):
+        L.lbm_set_kernel(sim.h, L.LBM_KERNEL_PAIRED)
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("nx,ny", [(37, 23), (130, 9), (2, 7)])
+def test_twopass_elementwise_2d(L, storage, nx, ny):
+    for eg, eh in elementwise(L, (ny, nx), L.LBM_KERNEL_TWOPASS, storage, seed=3 * nx + ny):
+        assert eg < TOL[storage] and eh < 3 * TOL[storage], (eg, eh)
+
+
+def test_twopass_walls(L):
+    for eg, eh in elementwise(L, (17, 37), L.LBM_KERNEL_TWOPASS, "fp32", walls=True, tau=0.8):
+        assert eg < 2e-6 and eh < 2e-6, (eg, eh)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("shape", [(9, 10, 11), (3, 5, 4)])
+def test_twopass_elementwise_3d(L, storage, shape):
+    # D3Q103, ragged; (3, 5, 4): every axis shorter than the stencil's reach
+    for eg, eh in elementwise(L, shape, L.LBM_KERNEL_TWOPASS, storage, steps=(1, 4), seed=sum(shape),
+                              lattice=2):
+        assert eg < TOL[storage] and eh < 3 * TOL[storage], (eg, eh)
+
+
+@pytest.mark.parametrize("shape", [(9, 10, 11), (3, 5, 4)])
+def test_direct_elementwise_3d(L, shape):
+    for eg, eh in elementwise(L, shape, L.LBM_KERNEL_DIRECT, "fp32", steps=(1, 4), seed=sum(shape), lattice=2):
+        assert eg < 2e-6 and eh < 2e-6, (eg, eh)
+
+
+def test_twopass_1000_steps_cfg0(L):
+    fields = inputs.shear_thermal_wave(64, 64, noise=1e-6, seed=0)
+    sim = L.Simulation(nx=64, ny=64, kernel=L.LBM_KERNEL_TWOPASS, **CFG0)
+    sim.init(*fields)
+    sim.step(1000)
+    mg = sim.moments()
+    sim.close()
+    o = O.Sim(O.D2Q37, nx=64, ny=64, **CFG0)
+    o.init(*fields)
+    o.step(1000)
+    mo = o.moments()
+    for k in ("rho", "u", "T"):
+        assert np.linalg.norm(mg[k] - mo[k]) <= 1e-5 * np.linalg.norm(mo[k]), k
