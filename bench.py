@@ -319,14 +319,14 @@ def bench_warm_start(lbm):
     """The learned warm start: surrogate trained on 256 steady channels (H 64..128), then
     256 held-out 4 x 256 channels from rest and from its prediction, to residual 1e-8."""
     from paper_1611_02409_gb300 import surrogate
-    res, _ = surrogate.study(lbm)
+    res, _ = surrogate.study(lbm, refine=False)
     t = res["test"]
     return {"workload": "256 held-out thermal Couette channels 4x256, seeded Pr, gamma, Ma, tau, dT; surrogate "
                         "5-512-512-512-512-1024 trained on 256 channels of height 64..128 by the lbm_mlp kernels",
             "steps_rest_median": t["steps_rest_median"], "steps_warm_median": t["steps_warm_median"],
             "step_ratio_median": t["step_ratio_median"], "batch_seconds_rest": t["batch_seconds_rest"],
             "batch_seconds_warm": t["batch_seconds_warm"], "converged": [t["rest_converged"], t["warm_converged"]],
-            "state_diff_at_1e8": t["state_diff_at_tol"], "state_diff_at_1e9": t["state_diff_at_tol_fine"],
+            "state_diff_at_1e8": t["state_diff_at_tol"],
             "train_seconds": res["train"]["seconds_total"], "final_loss": res["train"]["losses"][-1][1]}
 
 

@@ -158,7 +158,7 @@ def _summary(v):
 
 
 def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, max_steps=6_000_000,
-          check_every=200, train_H=(64, 128), iters=3000):
+          check_every=200, train_H=(64, 128), iters=3000, refine=True):
     """Trains on steady channels, then compares warm start and rest start on held-out
     4 x H channels: steps and batch wall time to residual `tol`, and the difference of
     the two converged states at `tol` and after both continue to `tol_fine`.  The
@@ -181,10 +181,15 @@ def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, 
                                         tol, max_steps, check_every)
     both = np.nonzero(rest["converged"] & warm["converged"])[0]
     du8, dT8 = state_diff(f_warm, f_rest, both)
-    rest9, f_rest9 = continue_channels(b_rest, n_test, tol_fine, max_steps, check_every)
-    warm9, f_warm9 = continue_channels(b_warm, n_test, tol_fine, max_steps, check_every)
-    b_rest.close()
-    b_warm.close()
+    if not refine:   # steps and wall time to tol only
+        b_rest.close()
+        b_warm.close()
+        rest9, f_rest9, warm9, f_warm9 = rest, f_rest, warm, f_warm
+    else:
+        rest9, f_rest9 = continue_channels(b_rest, n_test, tol_fine, max_steps, check_every)
+        warm9, f_warm9 = continue_channels(b_warm, n_test, tol_fine, max_steps, check_every)
+        b_rest.close()
+        b_warm.close()
     both9 = np.nonzero(rest9["converged"] & warm9["converged"])[0]
     du9, dT9 = state_diff(f_warm9, f_rest9, both9)
     # how far each tol-state still was from the tol_fine state of the same run
@@ -211,7 +216,7 @@ def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, 
                   batch_seconds_rest=rest["seconds"], batch_seconds_warm=warm["seconds"],
                   batch_steps_rest=rest["batch_steps"], batch_steps_warm=warm["batch_steps"],
                   state_diff_at_tol=dict(u=_summary(du8), T=_summary(dT8)),
-                  both_converged_fine=int(len(both9)),
+                  refined=bool(refine), both_converged_fine=int(len(both9)),
                   extra_steps_fine_median=dict(rest=float(np.median(rest9["steps"] - rest["steps"])),
                                                warm=float(np.median(warm9["steps"] - warm["steps"]))),
                   state_diff_at_tol_fine=dict(u=_summary(du9), T=_summary(dT9)),

@@ -80,9 +80,11 @@ def test_couette_grid_h256(L):
     for i, c in enumerate(cases):
         eta, u_an, T_an, heat = analytic(c, 256)
         U, dT = c["inputs"][2], c["inputs"][4]
-        # at residual 1e-8 the velocity mode is still ~1e-8 x its decay time (3e-3) away
-        for prof, utol in ((out["profiles_at_tol"][i], 1e-2), (out["profiles_settled"][i], 2e-3)):
+        # at residual 1e-8 the velocity mode is still ~1e-8 x its decay time (3e-3) away,
+        # and the Pr = 2 thermal mode (decay time 6.6e5 steps) only about three decay
+        # times in (a few % of dT); after settling, T is within 2 % of dT (the heating
+        # itself is 0.2-1.3 %)
+        for prof, utol, Ttol in ((out["profiles_at_tol"][i], 1e-2, 0.05), (out["profiles_settled"][i], 2e-3, 0.02)):
             u, T = prof
             assert np.abs(u - u_an).max() < utol * U, (i, np.abs(u - u_an).max() / U)
-            # within 2 % of the wall temperature difference (the heating itself is 0.2-1.3 %)
-            assert np.abs(T - T_an).max() < 0.02 * dT, (i, np.abs(T - T_an).max() / dT)
+            assert np.abs(T - T_an).max() < Ttol * dT, (i, np.abs(T - T_an).max() / dT)
