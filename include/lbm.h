@@ -74,9 +74,7 @@ extern "C" {
 #define LBM_KERNEL_PAIRED 3  /* two neighbouring cells per thread in packed FP32 pairs
                                 (D = 2, FP16 or BF16 storage, nx even)                 */
 #define LBM_KERNEL_TWOPASS 4 /* one cell per thread, populations read twice (moments,
-                                then relaxation) instead of held in registers; needs
-                                Q x (stored cells per plane) < 2^31; the default for
-                                D3Q103                                                 */
+                                then relaxation) instead of held in registers          */
 
 /* memory space of field pointers */
 #define LBM_MEM_DEVICE 0

@@ -71,8 +71,6 @@ template <int LAT, int ST> struct Launch {
     static bool tma_ok(const Ctx &c) { return c.kernel == 2 && staged_ok(c); }
     // two cells per thread: 2-D, 16-bit storage, even rows
     static bool paired_ok(const Ctx &c) { return Lattice<LAT>::D == 2 && ST != ST_FP32 && c.nx % 2 == 0; }
-    // two-pass gather: one population set (Q planes) addressed with 32-bit offsets
-    static bool twopass_ok(const Ctx &c) { return (long long)Lattice<LAT>::Q * c.plane < (1LL << 31); }
     template <bool W> static void step_tma(const Ctx &c, const KParams<LAT> &kp, const void *src, void *dst,
                                            cudaStream_t st)
     {
@@ -172,7 +170,6 @@ template <int LAT, int ST> Ops make_ops_st()
     o.set_pops = &Launch<LAT, ST>::set_pops;
     o.staged_ok = &Launch<LAT, ST>::staged_ok;
     o.paired_ok = &Launch<LAT, ST>::paired_ok;
-    o.twopass_ok = &Launch<LAT, ST>::twopass_ok;
     return o;
 }
 

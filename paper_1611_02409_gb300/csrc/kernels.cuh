@@ -179,9 +179,7 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
 }
 
 // Populations read from the source buffer where they are used (two-pass kernel): a cell's
-// wrapped source columns, rows and planes for the displacements -3..3 are tabulated once,
-// and a population's source is its set's base (g or h) plus the 32-bit element offset
-// I * plane + plane_z + row_y + col_x (one set spans < 2^31 elements: checked on the host).
+// wrapped source columns, rows and planes for the displacements -3..3 are tabulated once.
 // Opposite pairs are read in chunks of CH pairs: prefetch<P>() at the first pair of a
 // chunk issues the chunk's 4 CH loads (g and h of both members) into registers before any
 // of them is used, so each warp keeps a chunk of loads in flight; sv<I>() / tv<I>() then
@@ -194,8 +192,8 @@ template <int LAT, int ST, int CH> struct GatherPop {
     using T = typename S::T;
     static constexpr int Q = Lattice<LAT>::Q;
     static constexpr int NP = (Q - 1) / 2;
-    const T *gs, *hs;             // set bases: g planes, h planes
-    int plane;
+    const T *src;
+    long long plane;
     int col[7], row[7], pln[7];   // element offsets within a population plane
     mutable typename S::Raw bs[2 * CH], bt[2 * CH];
     template <int I> __device__ __forceinline__ int at() const
@@ -209,11 +207,10 @@ template <int LAT, int ST, int CH> struct GatherPop {
                 constexpr int k = decltype(KK)::value;
                 constexpr int I = 1 + 2 * (P + k);
                 if constexpr (P + k < NP) {
-                    const int o0 = I * plane + at<I>(), o1 = (I + 1) * plane + at<I + 1>();
-                    bs[2 * k] = S::raw(gs + o0);
-                    bs[2 * k + 1] = S::raw(gs + o1);
-                    bt[2 * k] = S::raw(hs + o0);
-                    bt[2 * k + 1] = S::raw(hs + o1);
+                    bs[2 * k] = S::raw(src + I * plane + at<I>());
+                    bs[2 * k + 1] = S::raw(src + (I + 1) * plane + at<I + 1>());
+                    bt[2 * k] = S::raw(src + (Q + I) * plane + at<I>());
+                    bt[2 * k + 1] = S::raw(src + (Q + I + 1) * plane + at<I + 1>());
                 }
             });
             asm volatile("" ::: "memory");
@@ -221,19 +218,15 @@ template <int LAT, int ST, int CH> struct GatherPop {
     }
     template <int I> __device__ __forceinline__ float sv() const
     {
-        if constexpr (I == 0) return S::ld(gs + at<0>());
+        if constexpr (I == 0) return S::ld(src + at<0>());
         else return S::cvt(bs[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
     template <int I> __device__ __forceinline__ float tv() const
     {
-        if constexpr (I == 0) return S::ld(hs + at<0>());
+        if constexpr (I == 0) return S::ld(src + Q * plane + at<0>());
         else return S::cvt(bt[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
-    __device__ __forceinline__ void refresh()
-    {
-        asm volatile("" : "+l"(gs));
-        asm volatile("" : "+l"(hs));
-    }
+    __device__ __forceinline__ void refresh() { asm volatile("" : "+l"(src)); }
 };
 
 // Pairs per prefetch chunk of the two-pass kernel: D2Q37's 18 pairs in two chunks,
@@ -258,9 +251,8 @@ __global__ void __launch_bounds__(128, twopass_min_blocks<LAT>()) k_stream_colli
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
     GatherPop<LAT, ST, twopass_chunk<LAT>()> pop;
-    pop.gs = src;
-    pop.hs = src + (long long)Lattice<LAT>::Q * kp.plane;
-    pop.plane = (int)kp.plane;
+    pop.src = src;
+    pop.plane = kp.plane;
     static_for<0, 7>([&](auto KK) {
         constexpr int C = decltype(KK)::value - 3;
         pop.col[KK] = wrap_sub<C>(x, kp.nx, small_x);

@@ -46,7 +46,7 @@ struct lbm_handle {
 static int default_kernel(const lbm_handle *h)
 {
     if (h->ops.paired_ok(h->ctx)) return LBM_KERNEL_PAIRED;
-    if (h->D == 3 && h->ops.twopass_ok(h->ctx)) return LBM_KERNEL_TWOPASS;
+    if (h->D == 3) return LBM_KERNEL_TWOPASS;
     return LBM_KERNEL_DIRECT;
 }
 
@@ -528,8 +528,6 @@ int lbm_set_kernel(lbm_handle *h, int variant)
         return set_err(h, LBM_ERR_ARG, "staged kernel needs D = 2 and nx a multiple of 128");
     if (variant == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx))
         return set_err(h, LBM_ERR_ARG, "paired kernel needs D = 2, 16-bit storage and nx even");
-    if (variant == LBM_KERNEL_TWOPASS && !h->ops.twopass_ok(h->ctx))
-        return set_err(h, LBM_ERR_ARG, "two-pass kernel needs Q x (cells per plane) < 2^31");
     if (variant < LBM_KERNEL_DIRECT || variant > LBM_KERNEL_TWOPASS) return set_err(h, LBM_ERR_ARG, "bad variant");
     h->ctx.kernel = variant;
     return LBM_OK;
@@ -546,7 +544,6 @@ int lbm_autotune(lbm_handle *h, int steps, int *chosen)
     for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_TWOPASS; ++v) {
         if (v == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx)) continue;
         if (v == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx)) continue;
-        if (v == LBM_KERNEL_TWOPASS && !h->ops.twopass_ok(h->ctx)) continue;
         h->ctx.kernel = v;
         int rc = lbm_step(h, 2);
         if (rc) return rc;

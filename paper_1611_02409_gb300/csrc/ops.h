@@ -30,7 +30,6 @@ struct Ops {
     void (*set_pops)(const Ctx &, void *buf, const double *g, const double *h, cudaStream_t);
     bool (*staged_ok)(const Ctx &);
     bool (*paired_ok)(const Ctx &);
-    bool (*twopass_ok)(const Ctx &);
 };
 
 Ops ops_d2q37_fp32();
