@@ -35,7 +35,7 @@ METRIC = "MLUPS & % HBM peak, FP32 vs FP16-store at ≤1e-3 err; warm-start step
 N_GRID = 4096
 PARAMS = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
 Q = 37
-KERNEL_SOURCES = ["kernels.cuh", "physics.cuh", "lattice.cuh", "dispatch.cuh", "tma_kernel.cuh"]
+KERNEL_SOURCES = ["kernels.cuh", "physics.cuh", "lattice.cuh", "dispatch.cuh", "tma_kernel.cuh", "vec2.cuh"]
 
 
 def workload(storage):

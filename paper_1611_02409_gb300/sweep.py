@@ -125,7 +125,7 @@ def run_couette(lbm, cases, tol=1e-8, settle_steps=0, check_every=1000, max_step
 
 
 def main():
-    """The full sweep: 256 squares + 256 channels, one batch, residual 1e-8 or 20k steps."""
+    """The sweep (default 256 squares + 256 channels), one batch, residual 1e-8 or 20k steps."""
     import argparse
     import json
     ap = argparse.ArgumentParser()
@@ -133,10 +133,12 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--squares", type=int, default=256)
+    ap.add_argument("--channels", type=int, default=256)
     a = ap.parse_args()
     from . import build, lbm
     build.build()
-    cases = draw_instances()
+    cases = draw_instances(a.squares, a.channels)
     ncomp = np.array([c["params"]["nx"] * (c["params"]["ny"] - (2 if c["kind"] == "channel" else 0))
                       for c in cases], dtype=np.float64)
     status, prof, xin, conv, secs = run_sweep(lbm, cases, max_steps=a.max_steps, tol=a.tol,
