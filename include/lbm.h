@@ -245,7 +245,8 @@ int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen);
  * Surrogate network (no paper counterpart: the learned warm start).  A multilayer
  * perceptron sizes[0] -> sizes[1] -> ... -> sizes[nlayers] with GELU on every hidden
  * layer and a linear output, trained on the mean squared error with Adam.  Products run
- * on the tensor cores in bfloat16 with FP32 accumulation; weights are kept in FP32.
+ * on the tensor cores in bfloat16 with FP32 accumulation (lbm_mlp_set_gemm); weights are
+ * kept in FP32.
  * Parameters are packed per layer as W (sizes[l] x sizes[l+1], row-major) then b.
  * All device work is queued on `stream`; calls that return host data synchronise.
  * --------------------------------------------------------------------------------- */
@@ -265,6 +266,17 @@ int lbm_mlp_forward(lbm_mlp *h, int batch, const float *x, float *y);
 int lbm_mlp_backward(lbm_mlp *h, const float *target, double *loss);
 /* One Adam step (Kingma & Ba, bias-corrected) with the last gradients. */
 int lbm_mlp_adam(lbm_mlp *h, float lr, float b1, float b2, float eps);
+
+/* Matrix-product form of the handle's products.  LBM_MLP_GEMM_TCGEN05 (the default):
+ * 128 x 64 output tiles as tcgen05 MMAs with operands staged in shared memory and the
+ * accumulator in tensor memory; LBM_MLP_GEMM_MMA_SYNC: warp-level mma.sync m16n8k16.
+ * Both take BF16 operands and accumulate in FP32.  A tcgen05 product whose completion
+ * wait times out (about a second) leaves its output unwritten and makes the next
+ * synchronising call (lbm_mlp_backward with a loss, lbm_mlp_get_params) return
+ * LBM_ERR_TIMEOUT. */
+#define LBM_MLP_GEMM_TCGEN05 0
+#define LBM_MLP_GEMM_MMA_SYNC 1
+int lbm_mlp_set_gemm(lbm_mlp *h, int kind);
 
 #ifdef __cplusplus
 }

@@ -1,8 +1,9 @@
 // Surrogate network kernels (include/lbm.h, lbm_mlp_*): a multilayer perceptron with
 // GELU hidden layers and a linear output, trained with the mean squared error and Adam.
-// Matrix products run on the tensor cores in bfloat16 with FP32 accumulation
-// (mma.sync m16n8k16); master weights, Adam moments, pre-activations and gradients are
-// FP32.  The operands held in bfloat16 are: the network input, the weights, every hidden
+// Matrix products run on the tensor cores in bfloat16 with FP32 accumulation: by
+// default as tcgen05 MMAs (operands staged in shared memory, the accumulator in tensor
+// memory), or as warp-level mma.sync m16n8k16 (lbm_mlp_set_gemm); master weights, Adam
+// moments, pre-activations and gradients are FP32.  The operands held in bfloat16 are: the network input, the weights, every hidden
 // activation fed to the next layer, and the backward deltas fed to the two gradient
 // products.  The GEMMs here are small (batch <= a few hundred, width <= 1024).
 #include <cuda_bf16.h>
@@ -113,6 +114,146 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
             }
 }
 
+// ---- tcgen05 form -------------------------------------------------------------------
+// One CTA (4 warps) computes a TM x TN tile of C.  Per K step of TK, the threads stage
+// op(A) (TM x TK) and op(B) (as TN rows of TK) in shared memory in the canonical
+// no-swizzle K-major layout: 8-row x 16-byte core matrices, row group by row group, so
+// K-adjacent core matrices are 128 bytes apart (the descriptors' leading byte offset) and
+// 8-row groups TK / 8 x 128 bytes apart (the stride byte offset).  One thread issues the
+// TK / 16 MMAs (M = 128, N = 64, K = 16, BF16 x BF16 -> FP32 in tensor memory) and commits
+// them to an mbarrier; every thread waits (bounded: on timeout the kernel sets *err and
+// leaves C unwritten) before the tiles are restaged.  The epilogue reads each thread's row
+// (TMEM lane) with tcgen05.ld and applies bias, GELU and the bfloat16 copy as k_gemm does.
+constexpr int TM = 128, TN = 64, TK = 64;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t core_off(int row, int k)
+{
+    return ((((row >> 3) * (TK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor: start, leading and stride byte offsets in 16-byte units,
+// descriptor version 1, no swizzling.
+__device__ __forceinline__ uint64_t mma_sdesc(uint32_t addr)
+{
+    constexpr uint32_t lbo = 128, sbo = (TK / 8) * 128;
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;  // about a second of SM clock
+    }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, int lda, int ta,
+                                                 const bf16 *__restrict__ B, int ldb, int tb, float *C, int ldc,
+                                                 const float *__restrict__ bias, int act, float *Cpre, bf16 *Cbf,
+                                                 int *err)
+{
+    __shared__ __align__(1024) unsigned char sA[TM * TK * 2];
+    __shared__ __align__(1024) unsigned char sB[TN * TK * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tbase)),
+                     "r"(TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+    // instruction descriptor: D FP32, A and B BF16, both K-major, N / 8, M / 16
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+    const bf16 zero = __float2bfloat16(0.f);
+    uint32_t phase = 0;
+    int ok = 1;
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        // consecutive threads take consecutive global addresses of each operand
+        for (int e = tid; e < TM * TK; e += 128) {
+            const int r = ta ? e % TM : e / TK, k = ta ? e / TM : e % TK, gm = m0 + r, gk = k0 + k;
+            const bf16 v = (gm < M && gk < K) ? (ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
+            *reinterpret_cast<bf16 *>(sA + core_off(r, k)) = v;
+        }
+        for (int e = tid; e < TN * TK; e += 128) {
+            const int r = tb ? e / TK : e % TN, k = tb ? e % TK : e / TN, gn = n0 + r, gk = k0 + k;
+            const bf16 v = (gn < N && gk < K) ? (tb ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn]) : zero;
+            *reinterpret_cast<bf16 *>(sB + core_off(r, k)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int s = 0; s < TK / 16; ++s) {
+                const uint64_t da = mma_sdesc(smem_addr(sA) + s * 256), db = mma_sdesc(smem_addr(sB) + s * 256);
+                const uint32_t accumulate = (k0 > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bar))
+                         : "memory");
+        }
+        const int w = mbar_wait_limit(&bar, phase) ? 1 : 0;
+        phase ^= 1;
+        ok = __syncthreads_and(w && ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+    }
+    if (ok) {
+        const int r = m0 + warp * 32 + (tid & 31);
+        for (int c = 0; c < TN; c += 8) {
+            uint32_t v[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = n0 + c + j;
+                if (r < M && col < N) {
+                    float x = __uint_as_float(v[j]) + (bias ? bias[col] : 0.f);
+                    const long long o = (long long)r * ldc + col;
+                    if (Cpre) Cpre[o] = x;
+                    if (act == 1) x = gelu_f(x);
+                    if (C) C[o] = x;
+                    if (Cbf) Cbf[o] = __float2bfloat16_rn(x);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+}
+
 __global__ void k_f2bf(const float *__restrict__ s, bf16 *d, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -199,6 +340,8 @@ struct lbm_mlp {
     float *dz = nullptr, *da = nullptr;
     bf16 *dzb = nullptr;
     double *partials = nullptr, *dloss = nullptr;
+    int *err = nullptr;             // set by a tcgen05 GEMM whose MMA wait timed out
+    int gemm_kind = LBM_MLP_GEMM_TCGEN05;
     int batch = 0;
     long long t = 0;
     cudaStream_t stream = nullptr;
@@ -217,11 +360,27 @@ int mfail(const char *msg) { return lbm::set_global_error(LBM_ERR_ARG, msg); }
 void gemm(lbm_mlp *h, int M, int N, int K, const bf16 *A, int lda, int ta, const bf16 *B, int ldb, int tb, float *C,
           int ldc, const float *bias, int act, float *Cpre, bf16 *Cbf)
 {
+    if (h->gemm_kind == LBM_MLP_GEMM_TCGEN05) {
+        dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+        k_gemm_tc<<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf, h->err);
+        return;
+    }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     k_gemm<<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf);
 }
 
 int grid1(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+// LBM_ERR_TIMEOUT once a tcgen05 GEMM gave up waiting for its MMAs (the word is then
+// cleared); call after a synchronisation of the handle's stream.
+int check_timeout(lbm_mlp *h)
+{
+    int e = 0;
+    LBM_MCK(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return LBM_OK;
+    LBM_MCK(cudaMemset(h->err, 0, sizeof(int)));
+    return lbm::set_global_error(LBM_ERR_TIMEOUT, "tcgen05 GEMM: MMA completion wait timed out");
+}
 
 } // namespace
 
@@ -267,6 +426,8 @@ int lbm_mlp_create(int nlayers, const int *sizes, int max_batch, void *stream, l
     al((void **)&h->dzb, sizeof(bf16) * (size_t)max_batch * maxn);
     al((void **)&h->partials, sizeof(double) * 4096);
     al((void **)&h->dloss, sizeof(double));
+    al((void **)&h->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         lbm_mlp_destroy(h);
         return lbm::set_global_error(LBM_ERR_NOMEM, cudaGetErrorString(e));
@@ -280,7 +441,8 @@ int lbm_mlp_destroy(lbm_mlp *h)
     if (!h) return LBM_OK;
     cudaStreamSynchronize(h->stream);
     for (void *p : {(void *)h->p, (void *)h->g, (void *)h->m, (void *)h->v, (void *)h->wb, (void *)h->xb,
-                    (void *)h->dz, (void *)h->da, (void *)h->dzb, (void *)h->partials, (void *)h->dloss})
+                    (void *)h->dz, (void *)h->da, (void *)h->dzb, (void *)h->partials, (void *)h->dloss,
+                    (void *)h->err})
         if (p) cudaFree(p);
     for (auto *p : h->z)
         if (p) cudaFree(p);
@@ -310,6 +472,14 @@ int lbm_mlp_get_params(lbm_mlp *h, float *params, float *grads)
     if (params) LBM_MCK(cudaMemcpyAsync(params, h->p, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
     if (grads) LBM_MCK(cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
     LBM_MCK(cudaStreamSynchronize(h->stream));
+    return check_timeout(h);
+}
+
+int lbm_mlp_set_gemm(lbm_mlp *h, int kind)
+{
+    if (!h) return mfail("null handle");
+    if (kind != LBM_MLP_GEMM_TCGEN05 && kind != LBM_MLP_GEMM_MMA_SYNC) return mfail("unknown GEMM kind");
+    h->gemm_kind = kind;
     return LBM_OK;
 }
 
@@ -361,6 +531,7 @@ int lbm_mlp_backward(lbm_mlp *h, const float *target, double *loss)
         LBM_MCK(cudaMemcpyAsync(&v, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         LBM_MCK(cudaStreamSynchronize(h->stream));
         *loss = v / (double)nout;
+        return check_timeout(h);
     }
     return LBM_OK;
 }

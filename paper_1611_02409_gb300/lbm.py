@@ -39,6 +39,8 @@ LBM_KERNEL_DIRECT = 1
 LBM_KERNEL_STAGED = 2
 LBM_KERNEL_PAIRED = 3
 LBM_KERNEL_TWOPASS = 4
+LBM_MLP_GEMM_TCGEN05 = 0
+LBM_MLP_GEMM_MMA_SYNC = 1
 LBM_MEM_DEVICE = 0
 LBM_MEM_HOST = 1
 
@@ -126,6 +128,7 @@ def lib():
             L.lbm_mlp_forward.argtypes = [vp, C.c_int, vp, vp]
             L.lbm_mlp_backward.argtypes = [vp, vp, dp]
             L.lbm_mlp_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
+            L.lbm_mlp_set_gemm.argtypes = [vp, C.c_int]
             L.lbm_field_totals_static.argtypes = [C.c_int, C.c_double, C.c_longlong, vp, vp, vp, vp, vp]
             L.lbm_autotune.argtypes = [vp, C.c_int, ip]
             _lib = L
@@ -439,7 +442,7 @@ class MLP:
     """GELU multilayer perceptron on the tensor cores (bfloat16 products, FP32 master
     weights); parameters exchanged as [[W (k x n), b (n)], ...] float arrays."""
 
-    def __init__(self, sizes, max_batch, stream=None):
+    def __init__(self, sizes, max_batch, stream=None, gemm=None):
         import torch
         self.torch = torch
         self.sizes = list(sizes)
@@ -449,6 +452,8 @@ class MLP:
         _check(lib().lbm_mlp_create(len(sizes) - 1, arr, int(max_batch), C.c_void_p(self.stream.cuda_stream),
                                     C.byref(self.h)))
         self.n = lib().lbm_mlp_num_params(self.h)
+        if gemm is not None:
+            _check(lib().lbm_mlp_set_gemm(self.h, int(gemm)))
 
     def _pack(self, params):
         return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in params]).astype(np.float32)

@@ -5,6 +5,7 @@ hold in bfloat16, so the remaining differences are FP32 accumulation order and t
 occasional bfloat16 rounding flip of a value that FP32 and FP64 place on opposite sides
 of a rounding boundary (2^-8 on that element): 2e-3 on outputs, 1e-2 on gradient norms.
 Against the unquantised FP64 network the bfloat16 operands themselves (2^-8) dominate.
+Both product forms are checked: tcgen05 MMAs (the default) and warp-level mma.sync.
 """
 import numpy as np
 import pytest
@@ -29,8 +30,15 @@ def relerr(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-@pytest.mark.parametrize("sizes,batch", [([5, 64, 48, 40], 37), ([5, 512, 512, 512, 512, 1024], 256)])
-def test_forward_and_gradients_match_reference(L, sizes, batch):
+GEMMS = [0, 1]  # LBM_MLP_GEMM_TCGEN05, LBM_MLP_GEMM_MMA_SYNC
+
+
+@pytest.mark.parametrize("gemm", GEMMS)
+@pytest.mark.parametrize("sizes,batch", [([5, 64, 48, 40], 37), ([5, 512, 512, 512, 512, 1024], 256),
+                                         ([5, 200, 130, 72], 300)])
+def test_forward_and_gradients_match_reference(L, sizes, batch, gemm):
+    # the last case is ragged in every product dimension against the 128 x 64 tcgen05
+    # tiles and their 64-wide K steps (batch 300 = 2 x 128 + 44; widths 200, 130, 72)
     import torch
     rng = np.random.default_rng(5)
     params = M.init_params(sizes, seed=11)
@@ -38,7 +46,7 @@ def test_forward_and_gradients_match_reference(L, sizes, batch):
         b[:] = rng.normal(size=b.shape) * 0.1
     x = rng.normal(size=(batch, sizes[0]))
     t = rng.normal(size=(batch, sizes[-1])) * 0.5
-    net = L.MLP(sizes, max_batch=batch)
+    net = L.MLP(sizes, max_batch=batch, gemm=gemm)
     net.set_params(params)
     params32 = [[W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)]
                 for W, b in params]
@@ -59,6 +67,30 @@ def test_forward_and_gradients_match_reference(L, sizes, batch):
     assert relerr(y, y64) < 3e-2
     for l in range(len(sizes) - 1):
         assert relerr(grads[l][0], g64[l][0]) < 5e-2
+    net.close()
+
+
+def test_gemm_forms_agree(L):
+    # the two product forms accumulate the same bfloat16 products in FP32 in different
+    # orders: outputs agree to FP32 accumulation roundoff
+    import torch
+    sizes = [5, 512, 512, 1024]
+    rng = np.random.default_rng(3)
+    params = M.init_params(sizes, seed=2)
+    x = torch.tensor(rng.normal(size=(128, 5)), dtype=torch.float32)
+    ys = []
+    for gemm in GEMMS:
+        net = L.MLP(sizes, max_batch=128, gemm=gemm)
+        net.set_params(params)
+        ys.append(net.forward(x).cpu().numpy())
+        net.close()
+    assert relerr(ys[0], ys[1]) < 1e-3
+
+
+def test_set_gemm_rejects_unknown_kind(L):
+    net = L.MLP([5, 8, 4], max_batch=4)
+    with pytest.raises(RuntimeError):
+        L._check(L.lib().lbm_mlp_set_gemm(net.h, 7))
     net.close()
 
 
@@ -83,13 +115,14 @@ def test_adam_step_matches_reference(L):
     net.close()
 
 
-def test_training_reduces_loss(L):
+@pytest.mark.parametrize("gemm", GEMMS)
+def test_training_reduces_loss(L, gemm):
     import torch
     sizes = [5, 64, 64, 8]
     rng = np.random.default_rng(9)
     x = rng.uniform(-1, 1, size=(256, 5))
     t = np.stack([np.sin(x @ rng.normal(size=5)) for _ in range(8)], axis=1)
-    net = L.MLP(sizes, max_batch=256)
+    net = L.MLP(sizes, max_batch=256, gemm=gemm)
     net.set_params(M.init_params(sizes, seed=1))
     xt, tt = torch.tensor(x, dtype=torch.float32), torch.tensor(t, dtype=torch.float32)
     losses = []
