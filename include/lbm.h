@@ -169,6 +169,14 @@ int lbm_set_kernel(lbm_handle *h, int variant);
  * the populations to the rest state (call before lbm_init_fields) and the step counter. */
 int lbm_autotune(lbm_handle *h, int steps, int *chosen);
 
+/* Fault injection for failure-detection tests (no paper counterpart).  on != 0: the
+ * staged kernel (LBM_KERNEL_STAGED) announces each tile's bytes but issues no copy, so its
+ * bounded waits run out (after ~2^22 SM cycles instead of ~2^31); the steps leave their
+ * output undefined and the next synchronising call (lbm_diagnostics, lbm_moments) returns
+ * LBM_ERR_TIMEOUT.  Nothing faults and the context stays usable; on = 0 restores normal
+ * operation (re-initialise the fields).  Other kernels ignore it.  Synchronises. */
+int lbm_debug_inject_stall(lbm_handle *h, int on);
+
 /* Conservation totals of caller-owned FP64 device fields, allocating nothing (the paper
  * has no counterpart: this serves callers that cannot call cudaMalloc, for instance code
  * whose device memory was all reserved up front by a host framework, or a time-critical
@@ -220,7 +228,9 @@ int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const doub
 
 /* Advances every active instance until all have converged (residual < tol at a check,
  * checks every `check_every` steps) or `max_steps` steps have been taken by the batch.
- * Synchronises.  *steps_taken (may be NULL) receives the number of batch steps run. */
+ * An instance whose fields turn non-finite stops at its next check with residual NaN
+ * (lbm_batch_status); the others carry on.  Synchronises.  *steps_taken (may be NULL)
+ * receives the number of batch steps run. */
 int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken);
 
 /* Per-instance status (host arrays of n entries, any may be NULL): steps taken, last

@@ -38,6 +38,8 @@
  *       wall values through the first fluid row, non-equilibrium part copied from the
  *       first fluid row (populations minus their own Maxwellian).
  *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta.
+ *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
+ *       stream in from outside the x range is the boundary cell's own of that velocity.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -48,7 +50,7 @@
 #define ORC_MAXN 8
 #define ORC_MAXT 6561 /* 3^8: largest D^n tensor held */
 
-enum { ORC_D2Q37 = 1, ORC_D3Q103 = 2 };
+enum { ORC_D2Q37 = 1, ORC_D3Q103 = 2, ORC_D2Q33 = 3 };
 enum { ORC_PR_SHIFTED = 0, ORC_PR_LITERAL = 1 };
 
 /* ------------------------------------------------------------------------- */
@@ -133,6 +135,10 @@ typedef struct {
 /* Generators of the velocity shells: every signed permutation of these. */
 static const int ORC_SHELLS_2D[8][3] = {
     {0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {3, 0, 0}, {3, 1, 0}, {3, 3, 0}};
+/* Table D2Q33 (Sec. VI B, Shim's lattice): (0,0), (1,0), (1,1), (2,0), (2,2), (3,0), (2,1),
+ * (4,4); its scale r is printed as 0.819381 sqrt(2). */
+static const int ORC_SHELLS_2D33[8][3] = {
+    {0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 2, 0}, {3, 0, 0}, {2, 1, 0}, {4, 4, 0}};
 static const int ORC_SHELLS_3D[10][3] = {
     {0, 0, 0}, {1, 0, 0}, {1, 1, 1}, {2, 0, 0}, {2, 1, 0}, {2, 2, 0}, {2, 2, 2}, {3, 0, 0}, {3, 1, 1}, {3, 3, 3}};
 
@@ -197,57 +203,64 @@ static void orc_shell_matrix(const orc_lattice *L, double r, int m, int (*a)[3],
         }
 }
 
-/* Builds the lattice: velocities from the shell generators; the scale r of D2Q37 is
- * the root of the determinant of the augmented degree-9 moment system (the system has
- * one more condition than shell weights, so it is consistent only at that r); the
- * shell weights are then its least-squares (= exact) solution.  D3Q103 reuses r. */
-static int orc_build_lattice(int lattice, orc_lattice *L)
+/* Root in [lo, hi] of the determinant of the augmented degree-9 moment system of a 2-D
+ * lattice of 8 shells (9 conditions, 8 shell weights: consistent only at that scale r),
+ * by bisection. */
+static double orc_solve_r(orc_lattice *L2, double lo, double hi)
 {
-    memset(L, 0, sizeof(*L));
     int (*a)[3] = malloc(sizeof(int[32][3]));
-    double rhs[32], M[16 * 16], Aug[16 * 16], ws[16];
-    /* D2Q37 first: it fixes r */
-    orc_lattice L2;
-    memset(&L2, 0, sizeof(L2));
-    L2.D = 2;
-    L2.nshell = 8;
-    for (int s = 0; s < 8; ++s) orc_add_shell(&L2, ORC_SHELLS_2D[s], s);
-    int m2 = orc_moment_conditions(2, a, rhs); /* 9 conditions, 8 unknowns */
-    double lo = 1.1, hi = 1.3, flo = 0, fhi = 0;
+    double rhs[32], M[16 * 16], Aug[16 * 16];
+    int m2 = orc_moment_conditions(2, a, rhs);
     for (int it = 0; it < 200; ++it) {
-        double rr[2] = {lo, hi}, f[2];
+        double rr[2] = {lo, 0.5 * (lo + hi)}, f[2];
         for (int k = 0; k < 2; ++k) {
-            orc_shell_matrix(&L2, rr[k], m2, a, M);
+            orc_shell_matrix(L2, rr[k], m2, a, M);
             for (int i = 0; i < m2; ++i) {
                 for (int j = 0; j < 8; ++j) Aug[i * 9 + j] = M[i * 8 + j];
                 Aug[i * 9 + 8] = rhs[i];
             }
             f[k] = orc_det(9, Aug);
         }
-        flo = f[0]; fhi = f[1];
-        double mid = 0.5 * (lo + hi);
-        orc_shell_matrix(&L2, mid, m2, a, M);
-        for (int i = 0; i < m2; ++i) {
-            for (int j = 0; j < 8; ++j) Aug[i * 9 + j] = M[i * 8 + j];
-            Aug[i * 9 + 8] = rhs[i];
-        }
-        double fm = orc_det(9, Aug);
-        if ((fm < 0) == (flo < 0)) lo = mid; else hi = mid;
+        if ((f[1] < 0) == (f[0] < 0)) lo = rr[1]; else hi = rr[1];
         if (hi - lo < 1e-15) break;
     }
-    (void)fhi;
-    double r = 0.5 * (lo + hi);
-    if (lattice == ORC_D2Q37) {
-        *L = L2;
-    } else if (lattice == ORC_D3Q103) {
-        L->D = 3;
-        L->nshell = 10;
-        for (int s = 0; s < 10; ++s) orc_add_shell(L, ORC_SHELLS_3D[s], s);
+    free(a);
+    return 0.5 * (lo + hi);
+}
+
+/* Builds the lattice: velocities from the shell generators; the scale r of a 2-D lattice
+ * is the root of the determinant of its augmented degree-9 moment system (D2Q37 in
+ * [1.1, 1.3]; D2Q33 in [1.14, 1.18], around its printed 0.819381 sqrt(2) = 1.15878); the
+ * shell weights are then the least-squares (= exact) solution.  D3Q103 reuses D2Q37's r. */
+static int orc_build_lattice(int lattice, orc_lattice *L)
+{
+    memset(L, 0, sizeof(*L));
+    double r;
+    if (lattice == ORC_D2Q33) {
+        L->D = 2;
+        L->nshell = 8;
+        for (int s = 0; s < 8; ++s) orc_add_shell(L, ORC_SHELLS_2D33[s], s);
+        r = orc_solve_r(L, 1.14, 1.18);
     } else {
-        free(a);
-        return -1;
+        orc_lattice L2;
+        memset(&L2, 0, sizeof(L2));
+        L2.D = 2;
+        L2.nshell = 8;
+        for (int s = 0; s < 8; ++s) orc_add_shell(&L2, ORC_SHELLS_2D[s], s);
+        r = orc_solve_r(&L2, 1.1, 1.3);
+        if (lattice == ORC_D2Q37) {
+            *L = L2;
+        } else if (lattice == ORC_D3Q103) {
+            L->D = 3;
+            L->nshell = 10;
+            for (int s = 0; s < 10; ++s) orc_add_shell(L, ORC_SHELLS_3D[s], s);
+        } else {
+            return -1;
+        }
     }
     L->r = r;
+    int (*a)[3] = malloc(sizeof(int[32][3]));
+    double rhs[32], M[16 * 16], ws[16];
     int m = orc_moment_conditions(L->D, a, rhs);
     orc_shell_matrix(L, r, m, a, M);
     orc_lstsq(m, L->nshell, M, rhs, ws);
@@ -514,6 +527,7 @@ typedef struct {
     orc_htab T;
     orc_coeffs k;
     int nx, ny, nz, walls, gh, nys; /* gh ghost rows beyond each wall row; nys stored rows */
+    int open_x;                     /* zero-gradient open ends in x (reading R16) */
     double uw[2][3], Tw[2];
     double *g, *h, *g2, *h2;        /* [stored cell][i] */
     long steps;
@@ -558,6 +572,12 @@ void *orc_create(int lattice, int nx, int ny, int nz, int walls, double Pr, doub
     S->g = calloc(n, sizeof(double)); S->h = calloc(n, sizeof(double));
     S->g2 = calloc(n, sizeof(double)); S->h2 = calloc(n, sizeof(double));
     return S;
+}
+
+int orc_set_open_x(void *p, int open)
+{
+    ((orc_sim *)p)->open_x = open ? 1 : 0;
+    return 0;
 }
 
 void orc_destroy(void *p)
@@ -679,7 +699,10 @@ int orc_step(void *p, int nsteps)
                 for (int x = 0; x < S->nx; ++x) {
                     for (int i = 0; i < Q; ++i) {
                         /* g_i(x + xi_i dt, t + dt) <- post-collision g_i(x, t): pull from x - c_i */
-                        int xs = orc_mod(x - S->L.c[i][0], S->nx);
+                        int xs = x - S->L.c[i][0];
+                        /* open ends: a population entering from outside the domain is the
+                         * boundary cell's own (zero-gradient) */
+                        xs = S->open_x ? (xs < 0 ? 0 : (xs > S->nx - 1 ? S->nx - 1 : xs)) : orc_mod(xs, S->nx);
                         int ys = S->walls ? y - S->L.c[i][1] : orc_mod(y - S->L.c[i][1], S->ny);
                         int zs = orc_mod(z - S->L.c[i][2], S->nz);
                         size_t c = orc_cell(S, xs, ys + S->gh, zs);

@@ -23,6 +23,7 @@ LIB = os.path.join(HERE, "liblbm_oracle.so")
 
 D2Q37 = 1
 D3Q103 = 2
+D2Q33 = 3
 PR_SHIFTED = 0
 PR_LITERAL = 1
 
@@ -53,6 +54,7 @@ def lib():
             L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]
             L.orc_destroy.argtypes = [C.c_void_p]
+            L.orc_set_open_x.argtypes = [C.c_void_p, C.c_int]
             L.orc_init.argtypes = [C.c_void_p, dp, dp, dp]
             L.orc_step.argtypes = [C.c_void_p, C.c_int]
             L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
@@ -140,7 +142,7 @@ class Sim:
     """One oracle simulation (periodic box, or 2-D channel with walls in y)."""
 
     def __init__(self, lattice_id=D2Q37, nx=16, ny=16, nz=1, walls=False, Pr=0.71, gamma=1.4,
-                 Nf=0.0, kappa=0.2, tau=0.6, mode=PR_SHIFTED, wall_u=None, wall_T=None):
+                 Nf=0.0, kappa=0.2, tau=0.6, mode=PR_SHIFTED, wall_u=None, wall_T=None, open_x=False):
         self.L = lib()
         self.D, self.r, self.c, self.w = lattice(lattice_id)
         self.nx, self.ny, self.nz = nx, ny, (nz if self.D == 3 else 1)
@@ -151,6 +153,8 @@ class Sim:
                                    mode, _dp(wu), _dp(wT))
         if not self.h:
             raise ValueError("oracle rejected the parameters")
+        if open_x:
+            self.L.orc_set_open_x(self.h, 1)
         self.coeffs = params(self.D, Pr, gamma, Nf, kappa, tau, mode)
 
     @property

@@ -34,7 +34,7 @@ struct lbm_handle {
     float *d_snap;         // u_x and T - 1 of the previous diagnostics call
     int have_snap;
     long long snap_step;
-    int *d_err;            // device error word of the kernels' bounded waits
+    int *d_err;            // [0] error word of the kernels' bounded waits, [1] fault injection
     double *d_stage;       // device staging for host-memory field I/O
     size_t stage_bytes;
     std::string err;
@@ -307,8 +307,8 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
     cudaDeviceGetAttribute(&h->ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
     h->ctx.kernel = default_kernel(h);
     cudaError_t e = cudaMalloc(&h->d_partials, sizeof(double) * lbm::kDiagNV * (h->diag_blocks + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), h->stream);
     if (e == cudaSuccess) h->ctx.d_err = h->d_err;
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_out, sizeof(double) * lbm::kDiagNV);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->buf_elems * h->elem, h->stream);
@@ -517,6 +517,15 @@ int lbm_diagnostics(lbm_handle *h, double *out)
     h->have_snap = 1;
     h->snap_step = h->steps;
     if (a[9] > 0) return set_err(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density / temperature");
+    return LBM_OK;
+}
+
+int lbm_debug_inject_stall(lbm_handle *h, int on)
+{
+    if (!h) return LBM_ERR_ARG;
+    const int v = on ? 1 : 0;
+    LBM_CK(h, cudaMemcpyAsync(h->d_err + 1, &v, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    LBM_CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 

@@ -158,11 +158,17 @@ __global__ void __launch_bounds__(256) k_bresid(Inst *inst, const KP *__restrict
         double t[4] = {0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x / 32); ++w)
             for (int v = 0; v < 4; ++v) t[v] += sh[w][v];
-        if (have) {
+        // a non-finite field makes its sums NaN (the comparisons below would read those as
+        // zero): report NaN and stop the instance
+        const bool bad = isnan(t[0]) || isnan(t[1]) || isnan(t[2]) || isnan(t[3]);
+        if (bad) {
+            d.residual = NAN;
+            d.active = 0;
+        } else if (have) {
             const double ru = t[1] > 0 ? sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
             const double rT = t[3] > 0 ? sqrt(t[2] / t[3]) : 0.0;
             d.residual = fmax(ru, rT) / m;
-            if (d.residual < tol || isnan(d.residual)) d.active = 0;  // converged, or diverged
+            if (d.residual < tol) d.active = 0;  // converged
         } else {
             d.residual = INFINITY;
             d.have_snap = 1;

@@ -61,12 +61,13 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^31 SM cycles (about a second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Bounded wait on an mbarrier phase: gives up after `limit` SM cycles (2^31, about a
+// second, unless a test asks for less).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit = 1LL << 31)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -126,6 +127,11 @@ __global__ void __launch_bounds__(128, tma_min_blocks<ST>()) k_stream_collide_tm
     const int lane = tx & 31, warp = tx >> 5;
     const int tpr = kp.nx / G::TW;  // tiles per row
     const bool small_y = kp.ny < 4;
+    // err[1] != 0: fault injection for the tests (lbm_debug_inject_stall): the producer
+    // announces a stage's bytes but issues no copy, so every wait runs out, after a short
+    // limit, and the launch reports LBM_ERR_TIMEOUT through err[0]
+    const bool stall = err[1] != 0;
+    const long long limit = stall ? (1LL << 22) : (1LL << 31);
 
     if (tx == 0) {
         mbar_init(&bar[0], 1);
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(128, tma_min_blocks<ST>()) k_stream_collide_tm
         T *sbase = stage0 + (size_t)st * STAGE_ELEMS;
         if (lane == 0) mbar_expect_tx(&bar[st], STAGE_BYTES);
         __syncwarp();
+        if (stall) return;
         const bool interior = x0 >= G::H && x0 + G::TW + G::H <= kp.nx;
         for (int p = lane; p < NP; p += 32) {
             const int i = p < Q ? p : p - Q;
@@ -178,13 +185,13 @@ __global__ void __launch_bounds__(128, tma_min_blocks<ST>()) k_stream_collide_tm
             fence_proxy_async();
             produce(tn, st ^ 1);
         }
-        const bool ok = mbar_wait_bounded(&bar[st], (k >> 1) & 1);
+        const bool ok = mbar_wait_bounded(&bar[st], (k >> 1) & 1, limit);
         if (!__syncthreads_and(ok)) {
             // record the failure, let the copies this block issued land (bounded), leave
             if (tx == 0) {
                 atomicExch(err, 1);
-                if (tn < ntiles) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1);
-                mbar_wait_bounded(&bar[st], (k >> 1) & 1);
+                if (tn < ntiles) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, limit);
+                mbar_wait_bounded(&bar[st], (k >> 1) & 1, limit);
             }
             __syncthreads();
             return;

@@ -111,6 +111,7 @@ def lib():
             L.lbm_get_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_populations.argtypes = [vp, vp, vp, C.c_int]
             L.lbm_set_kernel.argtypes = [vp, C.c_int]
+            L.lbm_debug_inject_stall.argtypes = [vp, C.c_int]
             L.lbm_batch_create.argtypes = [C.c_int, C.POINTER(lbm_params), C.POINTER(vp)]
             L.lbm_batch_destroy.argtypes = [vp]
             L.lbm_batch_init_fields.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]

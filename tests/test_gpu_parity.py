@@ -242,6 +242,55 @@ def test_full_size_sampled_one_step(L):
         assert abs(m["rho"][y, x].item() - st["rho"]) < 1e-6
         assert np.abs(m["u"][:, y, x].cpu().numpy() - st["u"]).max() < 1e-7
         assert abs(m["T"][y, x].item() - st["Teq"]) < 1e-6
+        # the stress is not conserved by the collision: it checks the relaxation itself
+        Pi = m["Pi"][:, y, x].cpu().numpy()
+        assert np.abs(Pi - post_collision_stress(o, go)).max() < 2e-6, (x, y)
+    del m
+    torch.cuda.synchronize()
+    sim.close()
+
+
+def post_collision_stress(o, go):
+    """Pi = sum_i g_i (xi_i - u)(xi_i - u), upper triangle (xx, xy, [xz,] yy, [yz, zz])."""
+    D = o.D
+    xi = o.r * np.asarray(o.c)[:, :D].astype(float)
+    rho = go.sum()
+    u = go @ xi / rho
+    d = xi - u
+    P = np.einsum("i,ia,ib->ab", go, d, d)
+    return np.array([P[a, b] for a in range(D) for b in range(a, D)])
+
+
+def test_full_size_3d_sampled_one_step(L):
+    # 256^3 D3Q103 thermal Taylor-Green in the benchmark's launch configuration (the
+    # default two-pass kernel, FP32): after one step, sampled cells (corners, seams and
+    # random ones) against the oracle's collision of the streamed initial equilibria
+    import torch
+    n = 256
+    rho, u, T = inputs.taylor_green_3d(n, U0=0.02, T_amp=0.01, noise=1e-6)
+    sim = L.Simulation(lattice=2, nx=n, ny=n, nz=n, **CFG0)
+    sim.init(rho, u, T)
+    sim.step(1)
+    m = sim.moments(device=True)
+    o = O.Sim(O.D3Q103, nx=4, ny=4, nz=4, **CFG0)
+    Nf = o.coeffs["Nf"]
+    rng = np.random.default_rng(1)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (2, n - 3, 1), (n // 2, 0, n - 1)] + \
+          [tuple(rng.integers(0, n, 3)) for _ in range(12)]
+    for (x, y, z) in pts:
+        g = np.zeros(len(o.c))
+        hh = np.zeros(len(o.c))
+        for i, cvec in enumerate(o.c):
+            xs, ys, zs = (x - cvec[0]) % n, (y - cvec[1]) % n, (z - cvec[2]) % n
+            G = O.equilibrium(O.D3Q103, rho[zs, ys, xs], u[:, zs, ys, xs], T[zs, ys, xs] * np.eye(3))
+            g[i] = G[i]
+            hh[i] = 0.5 * Nf * T[zs, ys, xs] * G[i]
+        go, ho = o.collide_cell(g, hh)
+        st = o.cell_state(go, ho)
+        assert abs(m["rho"][z, y, x].item() - st["rho"]) < 1e-6, (x, y, z)
+        assert np.abs(m["u"][:, z, y, x].cpu().numpy() - st["u"]).max() < 1e-7, (x, y, z)
+        assert abs(m["T"][z, y, x].item() - st["Teq"]) < 1e-6, (x, y, z)
+        assert np.abs(m["Pi"][:, z, y, x].cpu().numpy() - post_collision_stress(o, go)).max() < 2e-6, (x, y, z)
     del m
     torch.cuda.synchronize()
     sim.close()

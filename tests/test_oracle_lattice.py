@@ -1,4 +1,4 @@
-"""Pins of the oracle's lattices (Sec. VI, Table D2Q37; 3-D lattice reading R4).
+"""Pins of the oracle's lattices (Sec. VI, Tables D2Q37 and D2Q33; 3-D lattice reading R4).
 
 The oracle re-solves the D2Q37 shell weights and scale r in FP64.  They must round to the
 paper's printed 9-digit table, and both lattices must reproduce every moment of the unit
@@ -43,7 +43,28 @@ def _gauss_moment(alpha):
     return prod(0 if a % 2 else prod(range(a - 1, 0, -2)) for a in alpha)
 
 
-@pytest.mark.parametrize("which,Q", [(O.D2Q37, 37), (O.D3Q103, 103)])
+def test_d2q33_matches_printed_table():
+    # Table D2Q33: the 8 shells' 9 moment conditions fix r (a root of the augmented
+    # system's determinant) and the weights; they must round to the printed 6 digits
+    golden = os.path.join(os.path.dirname(__file__), "golden", "d2q33_table.txt")
+    rows, r_over = [], None
+    for line in open(golden):
+        if line.startswith("# r_over_sqrt2 "):
+            r_over = float(line.split()[2])
+        elif line.strip() and not line.startswith("#"):
+            cx, cy, k, wp = line.split()
+            rows.append((int(cx), int(cy), int(k), float(wp)))
+    D, r, c, w = O.lattice(O.D2Q33)
+    assert D == 2 and len(c) == 33 == sum(k for _, _, k, _ in rows)
+    assert abs(r / np.sqrt(2) - r_over) < 5e-7          # printed to 6 digits
+    assert np.abs(c).max() == 4
+    for cx, cy, k, wp in rows:
+        sel = [i for i in range(33) if sorted(map(abs, c[i, :2])) == sorted((cx, cy))]
+        assert len(sel) == k
+        assert np.allclose(w[sel], wp, rtol=6e-6, atol=0), (cx, cy, w[sel][0], wp)
+
+
+@pytest.mark.parametrize("which,Q", [(O.D2Q37, 37), (O.D3Q103, 103), (O.D2Q33, 33)])
 def test_lattice_moments_degree9(which, Q):
     D, r, c, w = O.lattice(which)
     assert len(c) == Q and np.all(w > 0)
@@ -65,11 +86,11 @@ def test_d2q37_is_not_exact_at_degree_10():
 
 
 def test_lattice_velocity_set_symmetric():
-    for which in (O.D2Q37, O.D3Q103):
+    for which, reach in ((O.D2Q37, 3), (O.D3Q103, 3), (O.D2Q33, 4)):
         D, r, c, w = O.lattice(which)
         vs = {tuple(v) for v in c}
         assert len(vs) == len(c)
         for i, v in enumerate(c):
             j = [k for k in range(len(c)) if tuple(c[k]) == tuple(-v)][0]
             assert w[i] == pytest.approx(w[j], rel=1e-14)
-        assert np.abs(c).max() == 3
+        assert np.abs(c).max() == reach
