@@ -344,6 +344,44 @@ def bench_warm_start(lbm):
             "train_seconds": res["train"]["seconds_total"], "final_loss": res["train"]["losses"][-1][1]}
 
 
+def bench_shock_tube(torch, lbm, peak, steps_tp=100):
+    """D2Q33 (Table D2Q33): the 1-D shock tube of Sec. VI B (1000 x 16, open x ends, 174
+    steps) against the exact Riemann solution, and D2Q33 throughput on the 4096^2 thermal
+    Taylor-Green field (FP32, direct kernel)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import riemann
+    from paper_1611_02409_gb300 import inputs
+    X, ny, steps = 1000, 16, 174
+    prm = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=2.0 / 3.0)
+    sim = lbm.Simulation(lattice=lbm.LBM_D2Q33, nx=X, ny=ny, bc_x=lbm.LBM_OPEN, **prm)
+    rho0 = np.where(np.arange(X) < X // 2, 4.0, 1.0)[None, :].repeat(ny, 0)
+    sim.init(rho0, np.zeros((2, ny, X)), np.ones((ny, X)))
+    sim.step(steps)
+    m = sim.moments()
+    r = sim.r
+    sim.close()
+    t = steps / (X * r)
+    s = (np.arange(X) + 0.5 - X / 2) / X / t
+    ex = riemann.sample(s, (4.0, 0.0, 4.0), (1.0, 0.0, 1.0), 1.4)
+    rho, u, p = m["rho"].mean(0), m["u"][0].mean(0), (m["rho"] * m["T"]).mean(0)
+    out = {"workload": "shock tube 1000x16, D2Q33, open x ends, (rho,T,u) = (4,1,0) | (1,1,0), gamma=1.4, "
+                       "tau=2/3, 174 steps (t = 0.150)",
+           "l1_rel_rho": float(np.abs(rho - ex[0]).mean() / 3), "l1_rel_u": float(np.abs(u - ex[1]).mean() / ex[1].max()),
+           "l1_rel_p": float(np.abs(p - ex[2]).mean() / 3), "t": t}
+    n = N_GRID
+    sim = lbm.Simulation(lattice=lbm.LBM_D2Q33, nx=n, ny=n, **PARAMS)
+    sim.init(*inputs.taylor_green_2d(n))
+    total_ms, launch_ms, _ = time_steps(torch, lbm, sim, steps_tp, 3, 1)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    b_cell = 2 * 33 * 2 * 4
+    ach = b_cell * n * n / (launch_ms * 1e-3) / 1e9
+    out["throughput_4096"] = {"mlups": n * n * steps_tp / (total_ms * 1e-3) / 1e6, "launch_ms": launch_ms,
+                              "algorithmic_bytes_per_cell": b_cell, "achieved_gbs": ach, "frac": ach / peak}
+    return out
+
+
 def _extra(out, name, fn):
     """One extra measurement; its failure is recorded, not raised."""
     t0 = time.perf_counter()
@@ -448,6 +486,7 @@ def run_ours(args):
         _extra(extra, "batched_sweep", lambda: bench_batch(torch, lbm, max(args.steps // 2, 100)))
         _extra(extra, "couette_grid", lambda: bench_couette(lbm))
         _extra(extra, "warm_start", lambda: bench_warm_start(lbm))
+        _extra(extra, "shock_tube_d2q33", lambda: bench_shock_tube(torch, lbm, peak))
         extra["cpu_baseline"] = oracle_mlups()
     if rank != 0:
         return

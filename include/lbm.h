@@ -46,6 +46,10 @@ extern "C" {
  * (shells 000,100,111,200,210,220,222,300,311,333 at the D2Q37 scale r) */
 #define LBM_D2Q37 1
 #define LBM_D3Q103 2
+/* Shim's D2Q33 (Sec. VI B, Table D2Q33: shells (0,0) (1,0) (1,1) (2,0) (2,2) (3,0) (2,1)
+ * (4,4), reach 4; the shock-tube lattice): its own scale r (the root of its degree-9
+ * moment system, printed as 0.819381 sqrt(2)); no walls; direct and two-pass kernels. */
+#define LBM_D2Q33 3
 
 /* parameter mapping (Sec. III Eq. Pr, Sec. V Eq. DiscreteReductionG):
  *   LBM_PR_SHIFTED: tau_s = tau, tau_q = (tau - 1/2)/Pr + 1/2, omega = 1/tau_q and the
@@ -65,6 +69,10 @@ extern "C" {
 /* y boundaries */
 #define LBM_PERIODIC 0
 #define LBM_WALLS 1 /* hybrid kinetic (KBC) + non-equilibrium extrapolation walls (Sec. VI A) */
+/* x boundaries (bc_x): periodic, or open ends (Sec. VI B, the shock tube) read as zero
+ * gradient: a population that would stream in from beyond x = 0 or x = nx - 1 is the
+ * boundary cell's own of that velocity */
+#define LBM_OPEN 2
 
 /* stream-collide kernel variants (lbm_set_kernel / lbm_autotune) */
 #define LBM_KERNEL_AUTO 0    /* the library's default for the configuration            */
@@ -93,6 +101,7 @@ typedef struct lbm_params {
     int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D = 2 only); x (and z) periodic    */
     double wall_u[2][3];  /* bottom (y = 0) / top (y = ny-1) wall velocity (tangential x)   */
     double wall_T[2];     /* bottom / top wall temperature, > 0                            */
+    int bc_x;             /* LBM_PERIODIC (default, 0) or LBM_OPEN (D = 2)                 */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

@@ -17,6 +17,7 @@ template <int LAT> KParams<LAT> make_kparams(const Ctx &c)
     kp.nys = c.nys;
     kp.gh = c.gh;
     kp.y0 = c.walls ? 1 : 0;
+    kp.open_x = c.open_x;
     kp.ny_comp = c.walls ? c.ny - 2 : c.ny;
     kp.plane = c.plane;
     kp.omega = (float)c.omega;
@@ -66,11 +67,14 @@ template <int LAT, int ST> struct Launch {
     // shared-memory-staged path: 2-D, nx a multiple of the tile width
     static bool staged_ok(const Ctx &c)
     {
-        return Lattice<LAT>::D == 2 && c.nx % TileGeom<ST>::TW == 0 && c.d_err != nullptr;
+        return LAT == LAT_D2Q37 && !c.open_x && c.nx % TileGeom<ST>::TW == 0 && c.d_err != nullptr;
     }
     static bool tma_ok(const Ctx &c) { return c.kernel == 2 && staged_ok(c); }
     // two cells per thread: 2-D, 16-bit storage, even rows
-    static bool paired_ok(const Ctx &c) { return Lattice<LAT>::D == 2 && ST != ST_FP32 && c.nx % 2 == 0; }
+    static bool paired_ok(const Ctx &c)
+    {
+        return LAT == LAT_D2Q37 && !c.open_x && ST != ST_FP32 && c.nx % 2 == 0;
+    }
     template <bool W> static void step_tma(const Ctx &c, const KParams<LAT> &kp, const void *src, void *dst,
                                            cudaStream_t st)
     {
@@ -90,14 +94,14 @@ template <int LAT, int ST> struct Launch {
     static void step(const Ctx &c, const void *src, void *dst, cudaStream_t st)
     {
         const KParams<LAT> kp = make_kparams<LAT>(c);
-        if constexpr (Lattice<LAT>::D == 2) {
+        if constexpr (LAT == LAT_D2Q37) {
             if (tma_ok(c)) {
                 if (c.walls) step_tma<true>(c, kp, src, dst, st);
                 else step_tma<false>(c, kp, src, dst, st);
                 return;
             }
         }
-        if constexpr (Lattice<LAT>::D == 2 && ST != ST_FP32) {
+        if constexpr (LAT == LAT_D2Q37 && ST != ST_FP32) {
             if (c.kernel == 3 && paired_ok(c)) {
                 const dim3 grid((c.nx / 2 + kTx - 1) / kTx, kp.ny_comp, 1);
                 const int sy = c.ny < 4;
@@ -110,8 +114,8 @@ template <int LAT, int ST> struct Launch {
         }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
         const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
-        // walls are 2-D only (the create call rejects them for D = 3): no 3-D wall kernels
-        constexpr bool W2 = Lattice<LAT>::D == 2;
+        // walls are D2Q37 only (the create call rejects them otherwise): no other wall kernels
+        constexpr bool W2 = LAT == LAT_D2Q37;
         if (c.kernel == 4) {
             if (W2 && c.walls)
                 k_stream_collide_2p<LAT, ST, W2><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
@@ -126,7 +130,7 @@ template <int LAT, int ST> struct Launch {
     }
     static void walls(const Ctx &c, void *buf, cudaStream_t st)
     {
-        if constexpr (Lattice<LAT>::D == 2) {
+        if constexpr (LAT == LAT_D2Q37) {
             WallParams wp;
             for (int b = 0; b < 2; ++b) {
                 for (int d = 0; d < 3; ++d) wp.vw[b][d] = (float)(c.wall_u[b][d] / c.r);

@@ -28,6 +28,17 @@ template <int C> __device__ __forceinline__ int wrap_sub(int x, int n, bool smal
     return v;
 }
 
+// Source column x - C of the gather: wrapped (periodic) or, with open ends, clamped to the
+// domain (zero gradient: a population from beyond an end is the end cell's own).
+template <int C> __device__ __forceinline__ int src_x(int x, int n, bool small, bool open)
+{
+    if (open) {
+        const int v = x - C;
+        return v < 0 ? 0 : (v >= n ? n - 1 : v);
+    }
+    return wrap_sub<C>(x, n, small);
+}
+
 template <int LAT>
 __device__ __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, int ys, int z)
 {
@@ -140,9 +151,10 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
     // a cell away from every periodic seam (|c| <= 3) gathers at fixed byte offsets; only
     // the warps holding the first and last three cells of a row diverge
-    bool interior = x >= 3 && x + 3 < kp.nx;
-    if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
-    if constexpr (D == 3) interior = interior && z >= 3 && z + 3 < kp.nz;
+    constexpr int R = Lattice<LAT>::R;
+    bool interior = x >= R && x + R < kp.nx;
+    if constexpr (!WALLS) interior = interior && y >= R && y + R < kp.ny;
+    if constexpr (D == 3) interior = interior && z >= R && z + R < kp.nz;
     typename S::Raw rs[Q], rt[Q];
     if (interior) {
         const char *base = reinterpret_cast<const char *>(src + o);
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
         static_for<0, Q>([&](auto II) {
             constexpr int I = decltype(II)::value;
             constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
-            const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+            const int xs = src_x<cx>(x, kp.nx, small_x, kp.open_x);
             int ys;
             if constexpr (WALLS) ys = y - cy + kp.gh;
             else ys = wrap_sub<cy>(y, kp.ny, small_y);
@@ -194,11 +206,12 @@ template <int LAT, int ST, int CH> struct GatherPop {
     static constexpr int NP = (Q - 1) / 2;
     const T *src;
     long long plane;
-    int col[7], row[7], pln[7];   // element offsets within a population plane
+    static constexpr int R = Lattice<LAT>::R;
+    int col[2 * R + 1], row[2 * R + 1], pln[2 * R + 1];   // element offsets within a plane
     mutable typename S::Raw bs[2 * CH], bt[2 * CH];
     template <int I> __device__ __forceinline__ int at() const
     {
-        return pln[cv<LAT, I, 2>() + 3] + row[cv<LAT, I, 1>() + 3] + col[cv<LAT, I, 0>() + 3];
+        return pln[cv<LAT, I, 2>() + R] + row[cv<LAT, I, 1>() + R] + col[cv<LAT, I, 0>() + R];
     }
     template <int P> __device__ __forceinline__ void prefetch() const
     {
@@ -253,9 +266,10 @@ __global__ void __launch_bounds__(128, twopass_min_blocks<LAT>()) k_stream_colli
     GatherPop<LAT, ST, twopass_chunk<LAT>()> pop;
     pop.src = src;
     pop.plane = kp.plane;
-    static_for<0, 7>([&](auto KK) {
-        constexpr int C = decltype(KK)::value - 3;
-        pop.col[KK] = wrap_sub<C>(x, kp.nx, small_x);
+    constexpr int R = Lattice<LAT>::R;
+    static_for<0, 2 * R + 1>([&](auto KK) {
+        constexpr int C = decltype(KK)::value - R;
+        pop.col[KK] = src_x<C>(x, kp.nx, small_x, kp.open_x);
         int ys;
         if constexpr (WALLS) ys = y - C + kp.gh;
         else ys = wrap_sub<C>(y, kp.ny, small_y);
@@ -313,11 +327,12 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
     if (x >= kp.nx) return;
     const int y = blockIdx.y + kp.y0;
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, 0);
-    // a block whose every source word (x - c_x - 1 .. x + 1 - c_x + 1, |c_x| <= 3) lies inside
+    // a block whose every source word (x - c_x - 1 .. x + 1 - c_x + 1, |c_x| <= R) lies inside
     // the row gathers at the fixed byte offsets
     const int xb = 2 * blockIdx.x * blockDim.x;
-    bool interior = xb >= 4 && xb + 2 * (int)blockDim.x + 4 <= kp.nx;
-    if constexpr (!WALLS) interior = interior && y >= 3 && y + 3 < kp.ny;
+    constexpr int R = Lattice<LAT>::R;
+    bool interior = xb >= R + 1 && xb + 2 * (int)blockDim.x + R + 1 <= kp.nx;
+    if constexpr (!WALLS) interior = interior && y >= R && y + R < kp.ny;
     // every load of the cell is issued before any word is combined (the byte permutes
     // and shifts wait for their loads): raw words first, then a compiler barrier
     uint32_t rs[Q], rt[Q], xs[Q], xt[Q];

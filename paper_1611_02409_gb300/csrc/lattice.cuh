@@ -4,6 +4,8 @@
 // (2,1), (3,0), (3,1), (3,3) and their signed permutations, xi_i = r c_i.
 // D3Q103: a degree-9 3-D lattice at the same scale (the paper gives none): shells
 // (0,0,0), (1,0,0), (1,1,1), (2,0,0), (2,1,0), (2,2,0), (2,2,2), (3,0,0), (3,1,1), (3,3,3).
+// D2Q33: Shim's lattice of Table D2Q33 (Sec. VI B, the shock tube): shells (0,0), (1,0),
+// (1,1), (2,0), (2,2), (3,0), (2,1), (4,4), at its own scale; reach 4.
 //
 // The order is the library's own: index 0 is the rest velocity, then opposite pairs
 // (2k+1, 2k+2) with c_{2k+2} = -c_{2k+1}, so a kernel evaluates the even and odd parts
@@ -17,11 +19,12 @@
 
 namespace lbm {
 
-enum : int { LAT_D2Q37 = 1, LAT_D3Q103 = 2 };
+enum : int { LAT_D2Q37 = 1, LAT_D3Q103 = 2, LAT_D2Q33 = 3 };
 
 template <int LAT> struct LatticeDims;
 template <> struct LatticeDims<LAT_D2Q37> { static constexpr int D = 2, Q = 37, NSHELL = 8; };
 template <> struct LatticeDims<LAT_D3Q103> { static constexpr int D = 3, Q = 103, NSHELL = 10; };
+template <> struct LatticeDims<LAT_D2Q33> { static constexpr int D = 2, Q = 33, NSHELL = 8; };
 
 struct VelTable {
     int c[128][3];
@@ -35,12 +38,15 @@ LBM_HD constexpr bool positive_rep(int x, int y, int z)
     return x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0)));
 }
 
-LBM_HD constexpr VelTable build_table(int D)
+LBM_HD constexpr VelTable build_table(int lat)
 {
     const int kShells2[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0},
                                 {2, 1, 0}, {3, 0, 0}, {3, 1, 0}, {3, 3, 0}};
     const int kShells3[10][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 1}, {2, 0, 0}, {2, 1, 0},
                                  {2, 2, 0}, {2, 2, 2}, {3, 0, 0}, {3, 1, 1}, {3, 3, 3}};
+    const int kShells33[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0},
+                                 {2, 2, 0}, {3, 0, 0}, {2, 1, 0}, {4, 4, 0}};
+    const int D = lat == LAT_D3Q103 ? 3 : 2;
     VelTable t{};
     t.Q = 1;
     t.c[0][0] = t.c[0][1] = t.c[0][2] = 0;
@@ -49,7 +55,8 @@ LBM_HD constexpr VelTable build_table(int D)
     const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     for (int s = 1; s < nsh; ++s) {
         int gen[3] = {0, 0, 0};
-        for (int d = 0; d < 3; ++d) gen[d] = D == 2 ? kShells2[s][d] : kShells3[s][d];
+        for (int d = 0; d < 3; ++d)
+            gen[d] = lat == LAT_D2Q33 ? kShells33[s][d] : (D == 2 ? kShells2[s][d] : kShells3[s][d]);
         const int np = D == 2 ? 2 : 6;
         for (int p = 0; p < np; ++p)
             for (int m = 0; m < (1 << D); ++m) {
@@ -74,11 +81,20 @@ LBM_HD constexpr VelTable build_table(int D)
     return t;
 }
 
+LBM_HD constexpr int max_reach(const VelTable &t)
+{
+    int r = 0;
+    for (int q = 0; q < t.Q; ++q)
+        for (int d = 0; d < 3; ++d) r = t.c[q][d] > r ? t.c[q][d] : r;
+    return r;
+}
+
 template <int LAT> struct Lattice {
     static constexpr int D = LatticeDims<LAT>::D;
     static constexpr int Q = LatticeDims<LAT>::Q;
     static constexpr int NSHELL = LatticeDims<LAT>::NSHELL;
-    static constexpr VelTable T = build_table(D);
+    static constexpr VelTable T = build_table(LAT);
+    static constexpr int R = max_reach(T);   // largest |c_i| component: the stencil's reach
     static_assert(T.Q == Q, "velocity count");
 };
 template <int LAT> constexpr VelTable Lattice<LAT>::T;

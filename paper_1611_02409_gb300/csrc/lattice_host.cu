@@ -7,7 +7,8 @@
 // (Sec. VI A prints r = 1.19697977): it is the root of the determinant of the augmented
 // 9 x 9 system [M(r) | b], found here by regula falsi (Illinois variant).  The weights
 // then solve the normal equations M^T M w = M^T b in extended precision.  The 3-D
-// lattice reuses that r (its 11 conditions in 10 shell weights are consistent there).
+// lattice reuses that r (its 11 conditions in 10 shell weights are consistent there);
+// D2Q33 (Table D2Q33, 8 shells, 9 conditions) has its own r, found the same way.
 #include <cmath>
 
 #include "lattice.cuh"
@@ -126,11 +127,13 @@ ld residual(const VelTable &t, int D, int nsh, const Conds &cd, int k, ld r, con
 
 int derive_lattice(int lattice, int (*c)[3], double *w, double *r_out)
 {
-    if (lattice != LAT_D2Q37 && lattice != LAT_D3Q103) return -1;
-    // scale r from the D2Q37 system
-    const VelTable t2 = build_table(2);
+    if (lattice != LAT_D2Q37 && lattice != LAT_D3Q103 && lattice != LAT_D2Q33) return -1;
+    // scale r from the 2-D system: D2Q37's (reused by D3Q103), or D2Q33's own (printed as
+    // 0.819381 sqrt(2) = 1.15878, Table D2Q33)
+    const bool q33 = lattice == LAT_D2Q33;
+    const VelTable t2 = build_table(q33 ? LAT_D2Q33 : LAT_D2Q37);
     const Conds c2 = conditions(2);
-    ld ra = 1.18L, rb = 1.21L;
+    ld ra = q33 ? 1.15L : 1.18L, rb = q33 ? 1.17L : 1.21L;
     ld fa = augmented_det(t2, 2, 8, c2, ra), fb = augmented_det(t2, 2, 8, c2, rb);
     if (!(fa * fb < 0)) return -1;
     int side = 0;
@@ -149,8 +152,8 @@ int derive_lattice(int lattice, int (*c)[3], double *w, double *r_out)
         }
     }
     const ld r = 0.5L * (ra + rb);
-    const int D = lattice == LAT_D2Q37 ? 2 : 3;
-    const VelTable t = build_table(D);
+    const int D = lattice == LAT_D3Q103 ? 3 : 2;
+    const VelTable t = build_table(lattice);
     const Conds cd = conditions(D);
     const int nsh = D == 2 ? 8 : 10;
     ld ws[16];

@@ -123,7 +123,7 @@ struct Mapped {
 // Validation and parameter mapping shared by lbm_create and lbm_map_params.
 static int map_params(const lbm_params &p, Mapped &m)
 {
-    if (p.lattice == LBM_D2Q37) m.D = 2;
+    if (p.lattice == LBM_D2Q37 || p.lattice == LBM_D2Q33) m.D = 2;
     else if (p.lattice == LBM_D3Q103) m.D = 3;
     else return set_err(nullptr, LBM_ERR_ARG, "unknown lattice");
     const int D = m.D;
@@ -131,8 +131,10 @@ static int map_params(const lbm_params &p, Mapped &m)
     if ((long long)p.nx * p.ny * (D == 3 ? p.nz : 1) > (1LL << 31) - 1)
         return set_err(nullptr, LBM_ERR_ARG, "grid too large");
     if (p.bc_y != LBM_PERIODIC && p.bc_y != LBM_WALLS) return set_err(nullptr, LBM_ERR_ARG, "bad bc_y");
-    if (p.bc_y == LBM_WALLS && (D != 2 || p.ny < 5))
-        return set_err(nullptr, LBM_ERR_ARG, "walls need D = 2 and ny >= 5");
+    if (p.bc_y == LBM_WALLS && (p.lattice != LBM_D2Q37 || p.ny < 5))
+        return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 and ny >= 5");
+    if (p.bc_x != LBM_PERIODIC && p.bc_x != LBM_OPEN) return set_err(nullptr, LBM_ERR_ARG, "bad bc_x");
+    if (p.bc_x == LBM_OPEN && D != 2) return set_err(nullptr, LBM_ERR_ARG, "open x ends need D = 2");
     if (p.storage < LBM_FP32 || p.storage > LBM_BF16) return set_err(nullptr, LBM_ERR_ARG, "bad storage");
     if (p.pr_mode != LBM_PR_SHIFTED && p.pr_mode != LBM_PR_LITERAL) return set_err(nullptr, LBM_ERR_ARG, "bad pr_mode");
     if (!(p.Pr > 0) || !(p.tau > 0.5) || !(p.kappa > 0) || !(p.kappa <= 1))
@@ -182,6 +184,7 @@ int make_ctx(const lbm_params &pin, Ctx &c, int *D_out, int *Q_out, double *r_ou
     memset(&c, 0, sizeof(c));
     c.storage = p.storage;
     c.walls = p.bc_y == LBM_WALLS;
+    c.open_x = p.bc_x == LBM_OPEN;
     c.nx = p.nx;
     c.ny = p.ny;
     c.nz = p.nz;
@@ -230,7 +233,7 @@ int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w)
     double ww[128], rr;
     int q = lbm::derive_lattice(lattice, cc, ww, &rr);
     if (q < 0) return set_err(nullptr, LBM_ERR_ARG, "unknown lattice");
-    if (D) *D = lattice == LBM_D2Q37 ? 2 : 3;
+    if (D) *D = lattice == LBM_D3Q103 ? 3 : 2;
     if (Q) *Q = q;
     if (r) *r = rr;
     for (int i = 0; i < q; ++i) {
@@ -271,6 +274,7 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
     memset(&c, 0, sizeof(c));
     c.storage = p.storage;
     c.walls = p.bc_y == LBM_WALLS;
+    c.open_x = p.bc_x == LBM_OPEN;
     c.nx = p.nx;
     c.ny = p.ny;
     c.nz = p.nz;
@@ -288,7 +292,7 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
         for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
         c.wall_T[b] = p.wall_T[b];
     }
-    h->ops = lbm::ops_for(D, p.storage);
+    h->ops = lbm::ops_for(p.lattice, p.storage);
     h->elem = p.storage == LBM_FP32 ? 4 : 2;
     h->buf_elems = (size_t)2 * h->Q * (size_t)c.plane;
     for (int k = 0; k < 2; ++k) {

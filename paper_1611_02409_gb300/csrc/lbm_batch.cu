@@ -326,9 +326,9 @@ int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out)
     size_t max_items = 0;
     for (int i = 0; i < n; ++i) {
         const lbm_params &p = params[i];
-        if (p.lattice != LBM_D2Q37 || p.storage != LBM_FP32) {
+        if (p.lattice != LBM_D2Q37 || p.storage != LBM_FP32 || p.bc_x != LBM_PERIODIC) {
             delete b;
-            return set_global_error(LBM_ERR_ARG, "batched instances are D2Q37 with FP32 storage");
+            return set_global_error(LBM_ERR_ARG, "batched instances are D2Q37, FP32 storage, periodic in x");
         }
         int D, Qd;
         double r;

@@ -12,6 +12,7 @@ struct Ctx {
     double w[128];
     double wall_u[2][3], wall_T[2];
     int *d_err;            // device error word (bounded waits that gave up set it)
+    int open_x;            // open (zero-gradient) x ends
     int num_sms;
     int kernel;            // 1 direct, 2 shared-memory staged
 };
@@ -38,11 +39,15 @@ Ops ops_d2q37_bf16();
 Ops ops_d3q103_fp32();
 Ops ops_d3q103_fp16();
 Ops ops_d3q103_bf16();
+Ops ops_d2q33_fp32();
+Ops ops_d2q33_fp16();
+Ops ops_d2q33_bf16();
 
-// The launch table of a lattice (2 = D2Q37, 3 = D3Q103 by dimension) and storage form.
-inline Ops ops_for(int D, int storage)
+// The launch table of a lattice (LBM_D2Q37 = 1, LBM_D3Q103 = 2, LBM_D2Q33 = 3) and storage form.
+inline Ops ops_for(int lattice, int storage)
 {
-    if (D == 2) return storage == 1 ? ops_d2q37_fp16() : storage == 2 ? ops_d2q37_bf16() : ops_d2q37_fp32();
+    if (lattice == 1) return storage == 1 ? ops_d2q37_fp16() : storage == 2 ? ops_d2q37_bf16() : ops_d2q37_fp32();
+    if (lattice == 3) return storage == 1 ? ops_d2q33_fp16() : storage == 2 ? ops_d2q33_bf16() : ops_d2q33_fp32();
     return storage == 1 ? ops_d3q103_fp16() : storage == 2 ? ops_d3q103_bf16() : ops_d3q103_fp32();
 }
 void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);

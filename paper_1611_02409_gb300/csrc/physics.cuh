@@ -98,6 +98,7 @@ template <int LAT> struct KParams {
     int nys;              // stored rows (ny + 2 gh)
     int gh;               // ghost rows beyond each wall row (0 when periodic)
     int y0, ny_comp;      // first computed domain row and number of computed rows
+    int open_x;           // open (zero-gradient) ends in x instead of periodic
     long long plane;      // stored cells per population plane
     float omega;          // relaxation rate
     float kappa, a_tr, a_sig; // Lambda = (1-k)[(1-nu) T_tr d + nu sigma] + k T_eq d

@@ -26,7 +26,7 @@ def test_exports_every_declared_symbol(L):
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103)])
+@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103), (3, O.D2Q33)])
 def test_library_lattice_matches_oracle(L, lat, olat):
     # two independent FP64 derivations of the same lattice must agree
     D, r, c, w = L.lbm_lattice_table(lat)
@@ -57,7 +57,8 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
                                  dict(gamma=2.5), dict(gamma=1.0), dict(nx=0), dict(bc_y=1, ny=4),
                                  dict(lattice=2, bc_y=1), dict(storage=9), dict(pr_mode=4),
                                  dict(kappa=1.0, Pr=0.71), dict(pr_mode=1, Pr=2.0, tau=0.9),
-                                 dict(bc_y=1, ny=16, wall_T=[1.0, -1.0])])
+                                 dict(bc_y=1, ny=16, wall_T=[1.0, -1.0]), dict(lattice=3, bc_y=1, ny=16),
+                                 dict(bc_x=5), dict(lattice=2, bc_x=2)])
 def test_invalid_parameters_rejected_without_gpu(L, bad):
     p = L.make_params(**bad)
     with pytest.raises(L.LbmError) as e:
