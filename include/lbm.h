@@ -98,7 +98,8 @@ typedef struct lbm_params {
     int pr_mode;          /* LBM_PR_SHIFTED or LBM_PR_LITERAL                              */
     int storage;          /* LBM_FP32, LBM_FP16 or LBM_BF16                                */
     int nx, ny, nz;       /* grid; nz = 1 for D = 2; nx, ny >= 1 (walls: ny >= 5)          */
-    int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D = 2 only); x (and z) periodic    */
+    int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D2Q37, D3Q103; walls are the planes
+                             y = 0 and y = ny - 1, z periodic)                            */
     double wall_u[2][3];  /* bottom (y = 0) / top (y = ny-1) wall velocity (tangential x)   */
     double wall_T[2];     /* bottom / top wall temperature, > 0                            */
     int bc_x;             /* LBM_PERIODIC (default, 0) or LBM_OPEN (D = 2)                 */

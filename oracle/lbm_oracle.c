@@ -36,7 +36,8 @@
  *       condition's flux balance, taken over the populations that cross in one step),
  *       equilibrium part G(rho_w, u, T delta) with u, T extrapolated linearly from the
  *       wall values through the first fluid row, non-equilibrium part copied from the
- *       first fluid row (populations minus their own Maxwellian).
+ *       first fluid row (populations minus their own Maxwellian).  In 3-D (D3Q103)
+ *       the same per wall column (x, z), periodic in x and z.
  *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta.
  *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
  *       stream in from outside the x range is the boundary cell's own of that velocity.
@@ -561,7 +562,8 @@ void *orc_create(int lattice, int nx, int ny, int nz, int walls, double Pr, doub
     orc_build_htab(&S->L, 4, &S->T);
     S->nx = nx; S->ny = ny; S->nz = S->L.D == 3 ? nz : 1;
     S->walls = walls;
-    if (walls && (S->L.D != 2 || ny < 5)) { orc_free_htab(&S->T); free(S); return NULL; }
+    /* walls: D2Q37 or D3Q103 (reach 3: two ghost rows beyond each wall row suffice) */
+    if (walls && (lattice == ORC_D2Q33 || ny < 5)) { orc_free_htab(&S->T); free(S); return NULL; }
     S->gh = walls ? 2 : 0;
     S->nys = ny + 2 * S->gh;
     for (int b = 0; b < 2; ++b) {
@@ -642,10 +644,12 @@ static void orc_walls(orc_sim *S, double *g, double *h)
         int n = b == 0 ? 1 : -1;               /* wall normal (y), into the fluid */
         int yw = b == 0 ? 0 : S->ny - 1;       /* wall row */
         int yn = yw + n;                       /* first fluid row */
-        #pragma omp parallel for schedule(static)
+        /* one wall column per (x, z) (z = 0 in 2-D) */
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int z = 0; z < S->nz; ++z)
         for (int x = 0; x < S->nx; ++x) {
             /* non-equilibrium of the first fluid row: populations minus their Maxwellian */
-            size_t cn1 = orc_cell(S, x, yn + S->gh, 0);
+            size_t cn1 = orc_cell(S, x, yn + S->gh, z);
             const double *gn = g + cn1 * Q, *hn = h + cn1 * Q;
             orc_state st;
             orc_moments_of(&S->L, &S->k, gn, hn, &st);
@@ -660,22 +664,23 @@ static void orc_walls(orc_sim *S, double *g, double *h)
                 Tk[kk] = S->Tw[b] - kk * (st.Teq - S->Tw[b]);
                 orc_maxwell_pops(S, 1.0, uk, Tk[kk], Gk[kk], Hk[kk]);
             }
-            /* mass leaving the fluid into column x's boundary rows: population i (moving
-             * toward the wall) from fluid rows 1..|c_iy| away from the wall */
+            /* mass leaving the fluid into column (x, z)'s boundary rows: population i
+             * (moving toward the wall) from fluid rows 1..|c_iy| away from the wall */
             double leaving = 0.0, A = 0.0, B = 0.0;
             for (int i = 0; i < Q; ++i) {
                 int cn = S->L.c[i][1] * n;
                 int xs = orc_mod(x - S->L.c[i][0], S->nx);
+                int zs = orc_mod(z - S->L.c[i][2], S->nz);
                 if (cn < 0)
                     for (int s = 1; s <= -cn; ++s)
-                        leaving += g[orc_cell(S, xs, yw + n * s + S->gh, 0) * Q + i];
+                        leaving += g[orc_cell(S, xs, yw + n * s + S->gh, zs) * Q + i];
                 /* mass the boundary rows k = 0..c_n-1 send into the fluid */
                 if (cn > 0)
                     for (int kk = 0; kk < cn; ++kk) { A += Gk[kk][i]; B += neq_g[i]; }
             }
             double rho_w = (leaving - B) / A;
             for (int kk = 0; kk <= S->gh; ++kk) {
-                size_t c = orc_cell(S, x, yw - n * kk + S->gh, 0);
+                size_t c = orc_cell(S, x, yw - n * kk + S->gh, z);
                 for (int i = 0; i < Q; ++i) {
                     g[c * Q + i] = rho_w * Gk[kk][i] + neq_g[i];
                     h[c * Q + i] = rho_w * Hk[kk][i] + neq_h[i];

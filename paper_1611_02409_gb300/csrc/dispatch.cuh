@@ -114,8 +114,8 @@ template <int LAT, int ST> struct Launch {
         }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
         const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
-        // walls are D2Q37 only (the create call rejects them otherwise): no other wall kernels
-        constexpr bool W2 = LAT == LAT_D2Q37;
+        // walls on D2Q37 and D3Q103 (reach 3); the create call rejects them for D2Q33
+        constexpr bool W2 = LAT != LAT_D2Q33;
         if (c.kernel == 4) {
             if (W2 && c.walls)
                 k_stream_collide_2p<LAT, ST, W2><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
@@ -130,13 +130,13 @@ template <int LAT, int ST> struct Launch {
     }
     static void walls(const Ctx &c, void *buf, cudaStream_t st)
     {
-        if constexpr (LAT == LAT_D2Q37) {
+        if constexpr (LAT != LAT_D2Q33) {
             WallParams wp;
             for (int b = 0; b < 2; ++b) {
                 for (int d = 0; d < 3; ++d) wp.vw[b][d] = (float)(c.wall_u[b][d] / c.r);
                 wp.thw[b] = (float)(c.wall_T[b] - 1.0);
             }
-            k_walls<LAT, ST><<<dim3((c.nx + 63) / 64, 2, 1), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), wp);
+            k_walls<LAT, ST><<<dim3((c.nx + 63) / 64, 2, c.nz), 64, 0, st>>>((T *)buf, make_kparams<LAT>(c), wp);
         }
     }
     static void moments(const Ctx &c, const void *buf, double *rho, double *u, double *T_, double *Pi, double *q,

@@ -509,19 +509,20 @@ struct WallParams {
     float thw[2];    // T_w - 1
 };
 
-// The wall procedure for one column x of wall b (0 bottom, 1 top) of buffer `buf`.
+// The wall procedure for one column (x, z) of wall b (0 bottom, 1 top) of buffer `buf`
+// (z = 0 in 2-D; in 3-D the walls are the planes y = 0 and y = ny - 1, periodic in x, z).
 template <int LAT, int ST>
 __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> &kp,
-                                            const WallParams &wp, int x, int b)
+                                            const WallParams &wp, int x, int b, int z = 0)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
-    static_assert(D == 2, "walls are 2-D");
+    static_assert(Lattice<LAT>::R <= 3, "two ghost rows beyond each wall row cover a reach of 3");
     const int n = b == 0 ? 1 : -1;
     const int yw = b == 0 ? 0 : kp.ny - 1;
-    const int small_x = kp.nx < 4;
+    const int small_x = kp.nx < 4, small_z = kp.nz < 4;
     float s1[Q], t1[Q];
-    load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, yw + n + kp.gh, 0), s1, t1);
+    load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, yw + n + kp.gh, z), s1, t1);
     RawMoments<D> m;
     raw_moments<LAT>(kp, ArrayPop{s1, t1}, m);
     CellState<D> c;
@@ -546,15 +547,16 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
     float Ld = 0.f, Bd = 0.f, Ad = 0.f, W = 0.f;
     static_for<0, Q>([&](auto II) {
         constexpr int I = decltype(II)::value;
-        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>();
+        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
         if constexpr (cy != 0) {
             const int cn = cy * n;
             const float w = kp.w[I];
             if (cn < 0) {
                 const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+                const int zs = D == 3 ? wrap_sub<cz>(z, kp.nz, small_z) : 0;
                 for (int sdist = 1; sdist <= -cn; ++sdist)
                     Ld = fmaf(w, Storage<ST>::ld(buf + (long long)I * kp.plane
-                                                 + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, 0)), Ld);
+                                                 + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, zs)), Ld);
             } else {
                 W = fmaf((float)cn, w, W);
                 Bd = fmaf((float)cn * w, s1[I], Bd);
@@ -565,7 +567,7 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
     const float drw = (Ld - Bd - Ad) / (W + Ad);   // rho_w - 1
     const float rw = 1.f + drw;
     for (int k = 0; k <= 2; ++k) {
-        const long long o = cell_index<LAT>(kp, x, yw - n * k + kp.gh, 0);
+        const long long o = cell_index<LAT>(kp, x, yw - n * k + kp.gh, z);
         // G(rho_w, u_k, T_k)/w - 1 = drw + rw * gk;   (N_f/2)(rho_w T_k G/w - 1) = drw' + rw * hk
         const float hb = kp.halfNf * drw;
 #pragma unroll
@@ -581,7 +583,7 @@ __global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
-    wall_column<LAT, ST>(buf, kp, wp, x, blockIdx.y);
+    wall_column<LAT, ST>(buf, kp, wp, x, blockIdx.y, blockIdx.z);
 }
 
 // Macroscopic fields of the stored populations (FP64 out, any pointer may be null).

@@ -131,8 +131,8 @@ static int map_params(const lbm_params &p, Mapped &m)
     if ((long long)p.nx * p.ny * (D == 3 ? p.nz : 1) > (1LL << 31) - 1)
         return set_err(nullptr, LBM_ERR_ARG, "grid too large");
     if (p.bc_y != LBM_PERIODIC && p.bc_y != LBM_WALLS) return set_err(nullptr, LBM_ERR_ARG, "bad bc_y");
-    if (p.bc_y == LBM_WALLS && (p.lattice != LBM_D2Q37 || p.ny < 5))
-        return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 and ny >= 5");
+    if (p.bc_y == LBM_WALLS && (p.lattice == LBM_D2Q33 || p.ny < 5))
+        return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 or D3Q103 and ny >= 5");
     if (p.bc_x != LBM_PERIODIC && p.bc_x != LBM_OPEN) return set_err(nullptr, LBM_ERR_ARG, "bad bc_x");
     if (p.bc_x == LBM_OPEN && D != 2) return set_err(nullptr, LBM_ERR_ARG, "open x ends need D = 2");
     if (p.storage < LBM_FP32 || p.storage > LBM_BF16) return set_err(nullptr, LBM_ERR_ARG, "bad storage");

@@ -55,7 +55,7 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
 
 @pytest.mark.parametrize("bad", [dict(lattice=7), dict(tau=0.5), dict(Pr=0.0), dict(kappa=0.0), dict(kappa=1.2),
                                  dict(gamma=2.5), dict(gamma=1.0), dict(nx=0), dict(bc_y=1, ny=4),
-                                 dict(lattice=2, bc_y=1), dict(storage=9), dict(pr_mode=4),
+                                 dict(storage=9), dict(pr_mode=4),
                                  dict(kappa=1.0, Pr=0.71), dict(pr_mode=1, Pr=2.0, tau=0.9),
                                  dict(bc_y=1, ny=16, wall_T=[1.0, -1.0]), dict(lattice=3, bc_y=1, ny=16),
                                  dict(bc_x=5), dict(lattice=2, bc_x=2)])

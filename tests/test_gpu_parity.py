@@ -150,6 +150,31 @@ def test_d3q103_parity(L):
         assert dev(mg[k], mo[k]) <= 1e-4, (k, dev(mg[k], mo[k]))
 
 
+@pytest.fixture(scope="module")
+def tgv32_500():
+    """The 3-D configuration's accuracy case: a 32^3 copy of the 256^3 thermal Taylor-Green
+    vortex, 500 steps on the oracle (computed once for both storage forms)."""
+    fields = inputs.taylor_green_3d(32, U0=0.02, T_amp=0.01, noise=1e-6)
+    o = O.Sim(O.D3Q103, nx=32, ny=32, nz=32, **CFG0)
+    o.init(*fields)
+    o.step(500)
+    mo = o.moments()
+    o.close()
+    return fields, mo
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16", 1e-3)])
+def test_d3q103_32cube_500_steps(L, tgv32_500, storage, tol):
+    fields, mo = tgv32_500
+    sim = L.Simulation(lattice=2, nx=32, ny=32, nz=32, storage=storage, **CFG0)   # default two-pass kernel
+    sim.init(*fields)
+    sim.step(500)
+    mg = sim.moments()
+    sim.close()
+    for k in ("rho", "u", "T"):
+        assert rel(mg[k], mo[k]) <= tol, (k, rel(mg[k], mo[k]))
+
+
 def test_nf_zero_and_literal_mode(L):
     # N_f = 0 (gamma = (D+2)/D: no energy populations) and the paper-literal mapping
     fields = inputs.shear_thermal_wave(16, 16, u_amp=0.02, T_amp=0.01, noise=0, seed=1)

@@ -142,3 +142,26 @@ def test_twopass_1000_steps_cfg0(L):
     mo = o.moments()
     for k in ("rho", "u", "T"):
         assert np.linalg.norm(mg[k] - mo[k]) <= 1e-5 * np.linalg.norm(mo[k]), k
+
+
+@pytest.mark.parametrize("kernel", [1, 4])
+def test_walls_3d_elementwise(L, kernel):
+    # D3Q103 channel with walls (planes y = 0, ny - 1), periodic in x and z
+    for eg, eh in elementwise(L, (3, 9, 4), kernel, "fp32", steps=(1, 4), walls=True, lattice=2, tau=0.8):
+        assert eg < 2e-6 and eh < 2e-6, (eg, eh)
+
+
+def test_walls_3d_couette_analytic(L):
+    # steady 3-D thermal Couette (Eq. CouetteDi3 with D = 3) on the GPU, default kernel
+    Ny, U, nx, nz = 33, 0.2, 4, 4
+    sim = L.Simulation(lattice=2, nx=nx, ny=Ny, nz=nz, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8, bc_y=1,
+                       wall_u=[[0, 0, 0], [U, 0, 0]], wall_T=[1.0, 1.01])
+    sim.init(np.ones((nz, Ny, nx)), np.zeros((3, nz, Ny, nx)), np.ones((nz, Ny, nx)))
+    sim.step(10000)
+    m = sim.moments()
+    sim.close()
+    yh = np.arange(Ny) / (Ny - 1)
+    heat = 0.71 * U ** 2 / (3 + sim.coeffs["Nf"] + 2)
+    Tan = 1.0 + 0.01 * yh + heat * yh * (1 - yh)
+    assert np.abs(m["u"][0].mean(axis=(0, 2)) - U * yh).max() < 1e-3 * U
+    assert np.abs(m["T"].mean(axis=(0, 2)) - Tan).max() < 0.1 * heat / 4

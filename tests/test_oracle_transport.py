@@ -169,3 +169,24 @@ def test_d3q103_shear_wave_viscosity():
     k = 2 * np.pi / N
     ratio = _fit_rate(ts, amps) / ((s.coeffs["tau_s"] - 0.5) / s.r ** 2 * k * k)
     assert abs(ratio - 1) < 1e-2, ratio
+
+
+def test_d3q103_couette_steady_profiles():
+    # 3-D walls (reading R5 per wall column (x, z)): steady thermal Couette on D3Q103 in a
+    # 1 x H x 1 column (exactly the x- and z-uniform flow), Eq. CouetteDi3 with D = 3
+    # (N_f = 2 for gamma = 1.4); u linear, T converging to the analytic profile
+    errs = []
+    for Ny, steps in [(17, 4000), (33, 10000)]:
+        U = 0.2
+        s = O.Sim(O.D3Q103, nx=1, ny=Ny, nz=1, walls=True, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8,
+                  wall_u=np.array([[0, 0, 0], [U, 0, 0]], float), wall_T=np.array([1.0, 1.01]))
+        s.init(np.ones((1, Ny, 1)), np.zeros((3, 1, Ny, 1)), np.ones((1, Ny, 1)))
+        s.step(steps)
+        m = s.moments()
+        yh = np.arange(Ny) / (Ny - 1)
+        heat = 0.71 * U ** 2 / (3 + s.coeffs["Nf"] + 2)
+        Tan = 1.0 + 0.01 * yh + heat * yh * (1 - yh)
+        assert np.abs(m["u"][0].ravel() - U * yh).max() < 1e-4 * U
+        assert np.abs(m["u"][1]).max() < 1e-4 * U and np.abs(m["u"][2]).max() < 1e-12
+        errs.append(np.abs(m["T"].ravel() - Tan).max() / (heat / 4))
+    assert errs[1] < 0.05 and errs[1] < 0.7 * errs[0], errs
