@@ -99,7 +99,9 @@ __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop 
     RawMoments<D, V> m;
     raw_moments<LAT, PRECISE>(kp, pop, m);
     CellState<D, V> c;
-    cell_state<LAT>(kp, m, c);
+    // packed lanes (16-bit storage) divide with the fast reciprocal; one-cell lanes keep
+    // IEEE division (on the 3-D two-pass kernel the fast form costs registers and spills)
+    cell_state<LAT, std::is_same<V, f2>::value>(kp, m, c);
     EqState<D, V> e;
     es_state<LAT>(kp, c, e);
     PolyCoef<D, V> pc;

@@ -16,6 +16,8 @@
 #include "../../include/lbm.h"
 #include "dispatch.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lbm {
 namespace batch {
 
@@ -449,7 +451,7 @@ int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const doub
     return LBM_OK;
 }
 
-int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken)
+static int batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken)
 {
     if (!b || max_steps < 0 || check_every < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
     int rc = ensure_graph(b, check_every, tol, b->tile);
@@ -464,6 +466,14 @@ int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int 
     }
     if (steps_taken) *steps_taken = done;
     return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken)
+{
+    nvtxRangePushA("lbm_batch_run");  // NVTX range over the whole run (profilers)
+    const int rc = batch_run(b, max_steps, tol, check_every, steps_taken);
+    nvtxRangePop();
+    return rc;
 }
 
 int lbm_batch_status(lbm_batch *b, int *steps, double *residual, int *active)

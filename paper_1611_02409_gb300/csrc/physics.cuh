@@ -400,14 +400,21 @@ template <int D, class V = float> struct CellState {
     V th_eq;              // T_eq - 1
 };
 
-template <int LAT, class V>
+// FASTDIV (the packed-lane collision of 16-bit storage): divisions by the fast reciprocal,
+// whose ~2-ulp error is far below the storage rounding (2^-11, 2^-8); otherwise IEEE division.
+template <class V> __device__ __forceinline__ V fast_inv(V x);
+template <> __device__ __forceinline__ float fast_inv<float>(float x) { return __fdividef(1.f, x); }
+template <> __device__ __forceinline__ f2 fast_inv<f2>(f2 x) { return f2(__fdividef(1.f, x.x), __fdividef(1.f, x.y)); }
+
+template <int LAT, bool FASTDIV = false, class V>
 __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMoments<Lattice<LAT>::D, V> &m,
                                            CellState<Lattice<LAT>::D, V> &c)
 {
     constexpr int D = Lattice<LAT>::D;
     c.drho = m.drho;
     c.rho = 1.f + m.drho;
-    c.inv_rho = 1.f / c.rho;
+    if constexpr (FASTDIV) c.inv_rho = fast_inv(c.rho);
+    else c.inv_rho = 1.f / c.rho;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         c.J[a] = m.J[a];
@@ -429,8 +436,13 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
         }
     c.rth_tr = tr * (1.f / D);
     if (kp.Nf > 0.f) {
-        c.rth_int = 2.f * m.H / kp.Nf - m.drho;
-        c.rth_eq = (D * c.rth_tr + kp.Nf * c.rth_int) / (D + kp.Nf);
+        if constexpr (FASTDIV) {
+            c.rth_int = __fdividef(2.f, kp.Nf) * m.H - m.drho;
+            c.rth_eq = (D * c.rth_tr + kp.Nf * c.rth_int) * __fdividef(1.f, D + kp.Nf);
+        } else {
+            c.rth_int = 2.f * m.H / kp.Nf - m.drho;
+            c.rth_eq = (D * c.rth_tr + kp.Nf * c.rth_int) / (D + kp.Nf);
+        }
         // T_rel = T_int + kappa (T_eq - T_int): equal to T_int at equilibrium whatever the
         // rounding of kappa
         c.rth_rel = vfma(kp.kappa, c.rth_eq - c.rth_int, c.rth_int);
