@@ -382,6 +382,30 @@ def bench_shock_tube(torch, lbm, peak, steps_tp=100):
     return out
 
 
+def bench_mode_study(lbm):
+    """Prandtl-number mappings (Sec. III; Sec. VI A): measured nu_kin, chi and Pr against tau
+    for the shifted and the literal mapping, and the paper's 50 x 400 Couette set-up
+    (u0 = 1, Pr = 1/1.4, tau = 1): start-up against the series, steady heating against
+    Eq. CouetteDi3."""
+    from paper_1611_02409_gb300 import mode_study as M
+    rows = M.transport_vs_tau(lbm)
+    out = {"workload": "shear and isobaric thermal waves, k = 2 pi/128, Pr = 1/1.4, gamma = 1.4, kappa = 0.2, "
+                       "FP32, one batch of 36; Couette 50x400 D2Q37, u0 = 1, tau = 1",
+           "transport": {m: {f"{r['tau']:g}": {"Pr_meas": r["Pr_meas"], "Pr_pred": r["Pr_pred"],
+                                              "nu_ratio": r["nu"] / r["nu_pred"], "chi_ratio": r["chi"] / r["chi_pred"]}
+                             for r in rows if r["mode"] == m} for m in ("shifted", "literal")}}
+    pc = M.paper_couette(lbm)
+    for m in ("shifted", "literal"):
+        st = pc[m]["steady"]
+        out[f"couette_{m}"] = {"Pr_eff": pc[m]["Pr_eff"],
+                               "startup_max_err": {f"t{p['t']:g}": p["max_err"] for p in pc[m]["startup"]},
+                               "steady_steps": st["steps"], "converged": st["converged"],
+                               "heating_ratio": st["heating_ratio"], "heating_ratio_set_Pr": st["heating_ratio_set_Pr"],
+                               "T_err": st["T_err"], "u_err": st["u_err"]}
+    out["couette_steady_seconds"] = pc["steady_seconds"]
+    return out
+
+
 def _extra(out, name, fn):
     """One extra measurement; its failure is recorded, not raised."""
     t0 = time.perf_counter()
@@ -487,6 +511,7 @@ def run_ours(args):
         _extra(extra, "couette_grid", lambda: bench_couette(lbm))
         _extra(extra, "warm_start", lambda: bench_warm_start(lbm))
         _extra(extra, "shock_tube_d2q33", lambda: bench_shock_tube(torch, lbm, peak))
+        _extra(extra, "mode_study", lambda: bench_mode_study(lbm))
         extra["cpu_baseline"] = oracle_mlups()
     if rank != 0:
         return

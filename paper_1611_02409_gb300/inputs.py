@@ -70,3 +70,16 @@ def random_fields(shape, seed=0, drho=0.02, du=0.03, dT=0.03):
 def rest_channel(nx=4, ny=256):
     """rho = 1, u = 0, T = 1 on an nx x ny channel (thermal Couette start)."""
     return np.ones((ny, nx)), np.zeros((2, ny, nx)), np.ones((ny, nx))
+
+
+def shear_wave(n=64, nx=4, amp=1e-3):
+    """rho = T = 1, u_x = amp sin(2 pi y/n), u_y = 0 on an nx x n periodic strip."""
+    y = np.arange(n, dtype=float)[:, None] * np.ones((1, nx))
+    return np.ones((n, nx)), np.stack([amp * np.sin(2 * np.pi * y / n), np.zeros((n, nx))]), np.ones((n, nx))
+
+
+def isobaric_thermal_wave(n=64, ny=4, amp=1e-3):
+    """T = 1 + amp sin(2 pi x/n), rho = 1/T (uniform pressure), u = 0 on an n x ny strip."""
+    x = np.arange(n, dtype=float)[None, :] * np.ones((ny, 1))
+    T = 1.0 + amp * np.sin(2 * np.pi * x / n)
+    return 1.0 / T, np.zeros((2, ny, n)), T

@@ -190,3 +190,36 @@ def test_d3q103_couette_steady_profiles():
         assert np.abs(m["u"][1]).max() < 1e-4 * U and np.abs(m["u"][2]).max() < 1e-12
         errs.append(np.abs(m["T"].ravel() - Tan).max() / (heat / 4))
     assert errs[1] < 0.05 and errs[1] < 0.7 * errs[0], errs
+
+
+@pytest.mark.parametrize("mode", [O.PR_SHIFTED, O.PR_LITERAL])
+def test_paper_couette_setup_startup_and_heating(mode):
+    # The paper's Couette set-up (Sec. VI A) at a reduced height: top wall at u0 = 1
+    # (Mach 0.85), kappa = 0.2, N_f = 3, Pr = 1/1.4 (the printed nu = 0.5 read as -0.5),
+    # tau = 1.  Start-up: Eq. CouetteVelocityDimensionless with nu_kin = (tau - 1/2)/r^2 at
+    # the paper's t = 5, 10 (t = steps / (r (Ny - 1))).  Steady heating: Eq. CouetteDi3
+    # with the mapping's Prandtl number, Pr itself when shifted and
+    # (tau - 1/2)/(tau/Pr - 1/2) = 0.556 for the literal mapping.
+    Ny, tau, Pr = 33, 1.0, 1.0 / 1.4
+    s = O.Sim(O.D2Q37, nx=4, ny=Ny, walls=True, Pr=Pr, gamma=1.4, kappa=0.2, tau=tau, mode=mode,
+              wall_u=np.array([[0, 0, 0], [1.0, 0, 0]]), wall_T=np.array([1.0, 1.0]))
+    s.init(np.ones((Ny, 4)), np.zeros((2, Ny, 4)), np.ones((Ny, 4)))
+    yh = np.arange(Ny) / (Ny - 1)
+    nu = (tau - 0.5) / s.r ** 2
+    n = np.arange(1, 400)[:, None]
+    done = 0
+    for t in (5.0, 10.0):
+        steps = int(round(t * s.r * (Ny - 1)))
+        s.step(steps - done)
+        done = steps
+        series = yh + 2 / np.pi * np.sum((-1.0) ** n / n * np.exp(-n ** 2 * np.pi ** 2 * nu * steps / (Ny - 1) ** 2)
+                                         * np.sin(n * np.pi * yh), axis=0)
+        assert np.abs(s.moments()["u"][0].mean(1) - series).max() < 3e-3, t
+    s.step(6000 - done)
+    T = s.moments()["T"].mean(1)
+    Pr_eff = Pr if mode == O.PR_SHIFTED else (tau - 0.5) / (tau / Pr - 0.5)
+    heat = Pr_eff / (2 + 3 + 2)
+    coef = np.polyfit(yh * (1 - yh), T - 1.0, 1)[0]
+    assert coef / heat == pytest.approx(1.0, abs=0.01)
+    if mode == O.PR_LITERAL:
+        assert coef / (Pr / 7) < 0.8  # the literal mapping's Prandtl number is off the set one
