@@ -17,6 +17,7 @@
  *   - Hermite polynomials H^(n)             Sec. IV, Grad's identities and the H^(0..6) list
  *   - Hermite coefficients a^(n)            Sec. IV, Eq. fESCoe (general term formula)
  *   - truncated Gaussian G^(4)              Sec. IV, Eq. GExpansion; discrete G_i of Sec. V
+ *     (G^(6), the Burnett order of Sec. IV, on the degree-13 D2Q77)
  *   - stream + collide                      Sec. V, Eq. DiscreteReductionG / DiscreteReductionH
  *   - lattices                              Sec. VI, Table D2Q37 (weights re-solved in FP64)
  *   - walls (hybrid KBC + NEEP)             Sec. VI A (prose only; reading below)
@@ -39,6 +40,10 @@
  *       first fluid row (populations minus their own Maxwellian).  In 3-D (D3Q103)
  *       the same per wall column (x, z), periodic in x and z.
  *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta.
+ *   R19 D2Q77 (shells 00,10,11,20,21,22,30,31,32,33,40,41,44,50,53; scale r the root of
+ *       its augmented degree-13 moment system) stands in for the degree-13 lattice that
+ *       the sixth-order expansion needs and the paper does not give; on it the
+ *       equilibrium is expanded to order 6.
  *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
  *       stream in from outside the x range is the boundary cell's own of that velocity.
  */
@@ -51,7 +56,7 @@
 #define ORC_MAXN 8
 #define ORC_MAXT 6561 /* 3^8: largest D^n tensor held */
 
-enum { ORC_D2Q37 = 1, ORC_D3Q103 = 2, ORC_D2Q33 = 3 };
+enum { ORC_D2Q37 = 1, ORC_D3Q103 = 2, ORC_D2Q33 = 3, ORC_D2Q77 = 4 };
 enum { ORC_PR_SHIFTED = 0, ORC_PR_LITERAL = 1 };
 
 /* ------------------------------------------------------------------------- */
@@ -140,6 +145,11 @@ static const int ORC_SHELLS_2D[8][3] = {
  * (4,4); its scale r is printed as 0.819381 sqrt(2). */
 static const int ORC_SHELLS_2D33[8][3] = {
     {0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 2, 0}, {3, 0, 0}, {2, 1, 0}, {4, 4, 0}};
+/* D2Q77 (reading R19): the paper prints no lattice for its sixth-order (Burnett) expansion;
+ * these 15 shells carry a positive-weight quadrature of degree 13 (even moments to 12). */
+static const int ORC_SHELLS_2D77[15][3] = {
+    {0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {2, 2, 0}, {3, 0, 0}, {3, 1, 0},
+    {3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 3, 0}};
 static const int ORC_SHELLS_3D[10][3] = {
     {0, 0, 0}, {1, 0, 0}, {1, 1, 1}, {2, 0, 0}, {2, 1, 0}, {2, 2, 0}, {2, 2, 2}, {3, 0, 0}, {3, 1, 1}, {3, 3, 3}};
 
@@ -168,16 +178,16 @@ static int orc_add_shell(orc_lattice *L, const int *gen, int shell_id)
     return 0;
 }
 
-/* Even multi-indices (a_1 >= ... >= a_D, sum <= 8) and (prod_d (a_d - 1)!!): the
- * moments E[xi^a] of the unit Gaussian that a degree-9 quadrature must reproduce;
- * odd moments vanish by the lattice's symmetry. */
-static int orc_moment_conditions(int D, int (*a)[3], double *rhs)
+/* Even multi-indices (a_1 >= ... >= a_D, sum <= maxdeg) and (prod_d (a_d - 1)!!): the
+ * moments E[xi^a] of the unit Gaussian that a quadrature of degree maxdeg + 1 must
+ * reproduce; odd moments vanish by the lattice's symmetry. */
+static int orc_moment_conditions(int D, int maxdeg, int (*a)[3], double *rhs)
 {
     int m = 0;
-    for (int a0 = 0; a0 <= 8; a0 += 2)
+    for (int a0 = 0; a0 <= maxdeg; a0 += 2)
         for (int a1 = 0; a1 <= a0; a1 += 2)
             for (int a2 = 0; a2 <= (D == 3 ? a1 : 0); a2 += 2) {
-                if (a0 + a1 + a2 > 8) continue;
+                if (a0 + a1 + a2 > maxdeg) continue;
                 a[m][0] = a0; a[m][1] = a1; a[m][2] = a2;
                 double v = 1.0;
                 int e[3] = {a0, a1, a2};
@@ -204,23 +214,26 @@ static void orc_shell_matrix(const orc_lattice *L, double r, int m, int (*a)[3],
         }
 }
 
-/* Root in [lo, hi] of the determinant of the augmented degree-9 moment system of a 2-D
- * lattice of 8 shells (9 conditions, 8 shell weights: consistent only at that scale r),
- * by bisection. */
-static double orc_solve_r(orc_lattice *L2, double lo, double hi)
+/* Root in [lo, hi] of the determinant of the augmented moment system of a 2-D lattice
+ * whose shells are one fewer than its moment conditions up to maxdeg (degree 9: 9
+ * conditions, 8 shells; degree 13: 16 conditions, 15 shells), consistent only at that
+ * scale r, by bisection.  Each condition is divided by its (positive) right-hand side. */
+static double orc_solve_r(orc_lattice *L2, int maxdeg, double lo, double hi)
 {
     int (*a)[3] = malloc(sizeof(int[32][3]));
-    double rhs[32], M[16 * 16], Aug[16 * 16];
-    int m2 = orc_moment_conditions(2, a, rhs);
+    double rhs[32], M[32 * 16], Aug[16 * 16];
+    int m2 = orc_moment_conditions(2, maxdeg, a, rhs);
+    const int ns = L2->nshell, n = ns + 1;
+    if (m2 != n) { free(a); return NAN; }
     for (int it = 0; it < 200; ++it) {
         double rr[2] = {lo, 0.5 * (lo + hi)}, f[2];
         for (int k = 0; k < 2; ++k) {
             orc_shell_matrix(L2, rr[k], m2, a, M);
             for (int i = 0; i < m2; ++i) {
-                for (int j = 0; j < 8; ++j) Aug[i * 9 + j] = M[i * 8 + j];
-                Aug[i * 9 + 8] = rhs[i];
+                for (int j = 0; j < ns; ++j) Aug[i * n + j] = M[i * ns + j] / rhs[i];
+                Aug[i * n + ns] = 1.0;
             }
-            f[k] = orc_det(9, Aug);
+            f[k] = orc_det(n, Aug);
         }
         if ((f[1] < 0) == (f[0] < 0)) lo = rr[1]; else hi = rr[1];
         if (hi - lo < 1e-15) break;
@@ -230,25 +243,34 @@ static double orc_solve_r(orc_lattice *L2, double lo, double hi)
 }
 
 /* Builds the lattice: velocities from the shell generators; the scale r of a 2-D lattice
- * is the root of the determinant of its augmented degree-9 moment system (D2Q37 in
- * [1.1, 1.3]; D2Q33 in [1.14, 1.18], around its printed 0.819381 sqrt(2) = 1.15878); the
- * shell weights are then the least-squares (= exact) solution.  D3Q103 reuses D2Q37's r. */
+ * is the root of the determinant of its augmented moment system (degree 9: D2Q37 in
+ * [1.1, 1.3]; D2Q33 in [1.14, 1.18], around its printed 0.819381 sqrt(2) = 1.15878;
+ * degree 13: D2Q77 in [0.96, 0.98], the only root in [0.8, 1.4]); the shell weights are
+ * then the least-squares (= exact) solution of the row-normalised conditions.  D3Q103
+ * reuses D2Q37's r. */
 static int orc_build_lattice(int lattice, orc_lattice *L)
 {
     memset(L, 0, sizeof(*L));
     double r;
+    int maxdeg = 8;
     if (lattice == ORC_D2Q33) {
         L->D = 2;
         L->nshell = 8;
         for (int s = 0; s < 8; ++s) orc_add_shell(L, ORC_SHELLS_2D33[s], s);
-        r = orc_solve_r(L, 1.14, 1.18);
+        r = orc_solve_r(L, 8, 1.14, 1.18);
+    } else if (lattice == ORC_D2Q77) {
+        L->D = 2;
+        L->nshell = 15;
+        for (int s = 0; s < 15; ++s) orc_add_shell(L, ORC_SHELLS_2D77[s], s);
+        maxdeg = 12;
+        r = orc_solve_r(L, 12, 0.96, 0.98);
     } else {
         orc_lattice L2;
         memset(&L2, 0, sizeof(L2));
         L2.D = 2;
         L2.nshell = 8;
         for (int s = 0; s < 8; ++s) orc_add_shell(&L2, ORC_SHELLS_2D[s], s);
-        r = orc_solve_r(&L2, 1.1, 1.3);
+        r = orc_solve_r(&L2, 8, 1.1, 1.3);
         if (lattice == ORC_D2Q37) {
             *L = L2;
         } else if (lattice == ORC_D3Q103) {
@@ -261,10 +283,14 @@ static int orc_build_lattice(int lattice, orc_lattice *L)
     }
     L->r = r;
     int (*a)[3] = malloc(sizeof(int[32][3]));
-    double rhs[32], M[16 * 16], ws[16];
-    int m = orc_moment_conditions(L->D, a, rhs);
+    double rhs[32], M[32 * 16], ones[32], ws[16];
+    int m = orc_moment_conditions(L->D, maxdeg, a, rhs);
     orc_shell_matrix(L, r, m, a, M);
-    orc_lstsq(m, L->nshell, M, rhs, ws);
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < L->nshell; ++j) M[i * L->nshell + j] /= rhs[i];
+        ones[i] = 1.0;
+    }
+    orc_lstsq(m, L->nshell, M, ones, ws);
     for (int q = 0; q < L->Q; ++q) L->w[q] = ws[L->shell[q]];
     free(a);
     return 0;
@@ -559,11 +585,13 @@ void *orc_create(int lattice, int nx, int ny, int nz, int walls, double Pr, doub
     orc_sim *S = calloc(1, sizeof(orc_sim));
     if (orc_build_lattice(lattice, &S->L)) { free(S); return NULL; }
     if (orc_map_params(S->L.D, Pr, gamma, Nf, kappa, tau, mode, &S->k)) { free(S); return NULL; }
-    orc_build_htab(&S->L, 4, &S->T);
+    /* the Hermite expansion's order: 4 (Eq. GExpansion) on the degree-9 lattices, 6 (the
+     * Burnett order, Sec. IV) on the degree-13 D2Q77 */
+    orc_build_htab(&S->L, lattice == ORC_D2Q77 ? 6 : 4, &S->T);
     S->nx = nx; S->ny = ny; S->nz = S->L.D == 3 ? nz : 1;
     S->walls = walls;
     /* walls: D2Q37 or D3Q103 (reach 3: two ghost rows beyond each wall row suffice) */
-    if (walls && (lattice == ORC_D2Q33 || ny < 5)) { orc_free_htab(&S->T); free(S); return NULL; }
+    if (walls && (lattice == ORC_D2Q33 || lattice == ORC_D2Q77 || ny < 5)) { orc_free_htab(&S->T); free(S); return NULL; }
     S->gh = walls ? 2 : 0;
     S->nys = ny + 2 * S->gh;
     for (int b = 0; b < 2; ++b) {

@@ -24,6 +24,7 @@ LIB = os.path.join(HERE, "liblbm_oracle.so")
 D2Q37 = 1
 D3Q103 = 2
 D2Q33 = 3
+D2Q77 = 4
 PR_SHIFTED = 0
 PR_LITERAL = 1
 

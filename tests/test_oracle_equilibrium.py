@@ -5,7 +5,9 @@
   prod_d He_{alpha_d}(xi_d), |alpha| <= 4, with the projections E[He_alpha] of the exact
   Gaussian computed by Gauss-Hermite quadrature.
 * Lattice moments of G_i up to order 4 equal the Gaussian's moments (rho, rho u,
-  rho(Lambda + uu), ...), which a degree-9 lattice integrates exactly.
+  rho(Lambda + uu), ...), which a degree-9 lattice integrates exactly.  On the degree-13
+  D2Q77 the sixth-order expansion (a^(5), a^(6) of Sec. IV) reproduces them up to order 6
+  and the fourth-order one does not.
 * Collision invariants: mass, momentum and total energy (reading R1, T_rel in the h
   target); equilibrium is a fixed point; the stress deviator and the translational-
   internal temperature gap relax at the rates the parameter mapping (reading R3) sets.
@@ -81,6 +83,40 @@ def test_equilibrium_moments_to_order4(which):
             assert abs(lat - ref) < 1e-12 * max(1, abs(ref)), (alpha, lat, ref)
 
 
+def _moment_errors(which, order, maxdeg, rho, u, Lam):
+    D, r, c, w = O.lattice(which)
+    xi = r * c[:, :D].astype(float)
+    G = O.equilibrium(which, rho, u, Lam, order=order)
+    out = {}
+    for deg in range(maxdeg + 1):
+        for a in range(deg + 1):
+            alpha = np.array((a, deg - a))
+            lat = np.sum(G * np.prod(xi ** alpha, axis=1))
+            ref = rho * gauss_expect(D, u, Lam, lambda x: np.prod(x ** alpha))
+            out[(a, deg - a)] = abs(lat - ref) / max(1, abs(ref))
+    return out
+
+
+def test_d2q77_sixth_order_moments():
+    # Sec. IV: the sixth-order expansion reproduces the Gaussian's moments up to order 6
+    # on a degree-13 lattice (6 + 6 <= 13); order 7 is beyond the truncation
+    rho, u, Lam = 0.93, np.array([0.35, -0.2]), spd(2, 0.2)
+    e6 = _moment_errors(O.D2Q77, 6, 7, rho, u, Lam)
+    assert max(v for k, v in e6.items() if sum(k) <= 6) < 1e-12, e6
+    assert max(v for k, v in e6.items() if sum(k) == 7) > 1e-6
+    # the fourth-order expansion on the same lattice misses orders 5 and 6
+    e4 = _moment_errors(O.D2Q77, 4, 6, rho, u, Lam)
+    assert max(v for k, v in e4.items() if sum(k) <= 4) < 1e-12
+    assert min(max(v for k, v in e4.items() if sum(k) == d) for d in (5, 6)) > 1e-5, e4
+
+
+def test_d2q77_equilibrium_vs_product_basis():
+    rho, u, Lam = 1.07, np.array([-0.25, 0.15]), spd(2)
+    G = O.equilibrium(O.D2Q77, rho, u, Lam, order=6)
+    ref = product_basis_equilibrium(O.D2Q77, rho, u, Lam, order=6)
+    assert np.allclose(G, ref, rtol=1e-11, atol=1e-16)
+
+
 def test_equilibrium_order4_truncation_differs_from_order6():
     # the fifth and sixth Hermite terms are dropped (Eq. GExpansion), so orders differ
     u, Lam = np.array([0.3, 0.1]), np.array([[1.1, 0.05], [0.05, 0.95]])
@@ -89,10 +125,11 @@ def test_equilibrium_order4_truncation_differs_from_order6():
     assert np.abs(G4 - G6).max() > 1e-6
 
 
-def _perturbed_state(sim, rho=1.05, u=(0.05, -0.03, 0.02), T=1.02, amp=2e-3):
+def _perturbed_state(sim, rho=1.05, u=(0.05, -0.03, 0.02), T=1.02, amp=2e-3, which=None):
     D = sim.D
     u = np.array(u[:D], float)
-    G = O.equilibrium(O.D2Q37 if D == 2 else O.D3Q103, rho, u, T * np.eye(D))
+    which = which or (O.D2Q37 if D == 2 else O.D3Q103)
+    G = O.equilibrium(which, rho, u, T * np.eye(D), order=6 if which == O.D2Q77 else 4)
     g = G * (1 + amp * rng.normal(size=G.size))
     h = 0.5 * sim.coeffs["Nf"] * T * G * (1 + amp * rng.normal(size=G.size))
     return g, h
@@ -103,13 +140,13 @@ def _invariants(sim, g, h):
     return np.concatenate([[g.sum()], g @ xi, [np.sum(0.5 * (xi ** 2).sum(1) * g) + h.sum()]])
 
 
-@pytest.mark.parametrize("which", [O.D2Q37, O.D3Q103])
+@pytest.mark.parametrize("which", [O.D2Q37, O.D3Q103, O.D2Q77])
 @pytest.mark.parametrize("Pr,gamma,kappa,mode", [(0.71, 1.4, 0.2, O.PR_SHIFTED), (2.0, 1.3, 0.5, O.PR_SHIFTED),
                                                  (0.71, 1.4, 0.2, O.PR_LITERAL), (1.0, 1.1, 0.9, O.PR_SHIFTED)])
 def test_collision_conserves_mass_momentum_energy(which, Pr, gamma, kappa, mode):
     sim = O.Sim(which, nx=4, ny=4, nz=4, Pr=Pr, gamma=gamma, kappa=kappa, tau=0.8, mode=mode)
     for _ in range(3):
-        g, h = _perturbed_state(sim)
+        g, h = _perturbed_state(sim, which=which)
         go, ho = sim.collide_cell(g, h)
         # FP64 sums of 2Q terms of size <= ~3: roundoff <= 2Q * 2^-53 * 3 (~7e-14 for Q = 103)
         tol = 2 * len(g) * 2.0 ** -53 * 3

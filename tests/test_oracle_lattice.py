@@ -86,7 +86,7 @@ def test_d2q37_is_not_exact_at_degree_10():
 
 
 def test_lattice_velocity_set_symmetric():
-    for which, reach in ((O.D2Q37, 3), (O.D3Q103, 3), (O.D2Q33, 4)):
+    for which, reach in ((O.D2Q37, 3), (O.D3Q103, 3), (O.D2Q33, 4), (O.D2Q77, 5)):
         D, r, c, w = O.lattice(which)
         vs = {tuple(v) for v in c}
         assert len(vs) == len(c)
@@ -94,3 +94,18 @@ def test_lattice_velocity_set_symmetric():
             j = [k for k in range(len(c)) if tuple(c[k]) == tuple(-v)][0]
             assert w[i] == pytest.approx(w[j], rel=1e-14)
         assert np.abs(c).max() == reach
+
+
+def test_d2q77_moments_degree13():
+    D, r, c, w = O.lattice(O.D2Q77)
+    assert len(c) == 77 and np.all(w > 0) and w.sum() == pytest.approx(1.0, abs=1e-14)
+    assert r == pytest.approx(0.9700084987393947, abs=1e-12)  # the only root in [0.8, 1.4]
+    xi = r * c[:, :2].astype(float)
+    for deg in range(14):
+        for a in range(deg + 1):
+            alpha = (a, deg - a)
+            m = np.sum(w * xi[:, 0] ** alpha[0] * xi[:, 1] ** alpha[1])
+            ref = _gauss_moment(alpha)
+            assert abs(m - ref) < 1e-10 * max(1, ref), (alpha, m, ref)
+    # degree 14 is not exact (so the check above is not vacuous)
+    assert abs(np.sum(w * xi[:, 0] ** 8 * xi[:, 1] ** 6) / _gauss_moment((8, 6)) - 1) > 1e-2
