@@ -382,6 +382,29 @@ def bench_shock_tube(torch, lbm, peak, steps_tp=100):
     return out
 
 
+def bench_burnett(torch, lbm, peak, steps=60):
+    """D2Q77 with the sixth-order (Burnett) equilibrium (Sec. IV): throughput of the default
+    two-pass kernel on the 4096^2 thermal Taylor-Green field, FP32 and FP16 storage, at
+    2 x 77 x 2 x 4 (FP32) / 2 bytes (FP16) algorithmic bytes per cell."""
+    from paper_1611_02409_gb300 import inputs
+    n = N_GRID
+    out = {"workload": "thermal Taylor-Green 4096x4096 periodic, D2Q77 (sixth-order equilibrium), Pr=0.71, "
+                       "gamma=1.4, kappa=0.2, tau=0.528655"}
+    fields = inputs.taylor_green_2d(n)
+    for st, elem in (("fp32", 4), ("fp16", 2)):
+        sim = lbm.Simulation(lattice=lbm.LBM_D2Q77, nx=n, ny=n, storage=st, **PARAMS)
+        sim.init(*fields)
+        total_ms, launch_ms, _ = time_steps(torch, lbm, sim, steps, 3, 1)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        b_cell = 2 * 77 * 2 * elem
+        ach = b_cell * n * n / (launch_ms * 1e-3) / 1e9
+        out[st] = {"mlups": n * n * steps / (total_ms * 1e-3) / 1e6, "launch_ms": launch_ms,
+                   "algorithmic_bytes_per_cell": b_cell, "achieved_gbs": ach, "frac": ach / peak, "steps": steps}
+    return out
+
+
 def bench_mode_study(lbm):
     """Prandtl-number mappings (Sec. III; Sec. VI A): measured nu_kin, chi and Pr against tau
     for the shifted and the literal mapping, and the paper's 50 x 400 Couette set-up
@@ -512,6 +535,7 @@ def run_ours(args):
         _extra(extra, "warm_start", lambda: bench_warm_start(lbm))
         _extra(extra, "shock_tube_d2q33", lambda: bench_shock_tube(torch, lbm, peak))
         _extra(extra, "mode_study", lambda: bench_mode_study(lbm))
+        _extra(extra, "burnett_d2q77", lambda: bench_burnett(torch, lbm, peak))
         extra["cpu_baseline"] = oracle_mlups()
     if rank != 0:
         return

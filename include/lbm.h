@@ -50,6 +50,13 @@ extern "C" {
  * (4,4), reach 4; the shock-tube lattice): its own scale r (the root of its degree-9
  * moment system, printed as 0.819381 sqrt(2)); no walls; direct and two-pass kernels. */
 #define LBM_D2Q33 3
+/* D2Q77, this library's degree-13 lattice for the sixth-order (Burnett) expansion of
+ * Sec. IV (a^(5), a^(6)), which the paper names but prints no lattice for: shells (0,0)
+ * (1,0) (1,1) (2,0) (2,1) (2,2) (3,0) (3,1) (3,2) (3,3) (4,0) (4,1) (4,4) (5,0) (5,3),
+ * reach 5, its own scale r = 0.97000849874 (the root of its degree-13 moment system); the
+ * equilibrium is expanded to order 6.  Periodic or open x ends, no walls; two-pass
+ * (default) and direct kernels. */
+#define LBM_D2Q77 4
 
 /* parameter mapping (Sec. III Eq. Pr, Sec. V Eq. DiscreteReductionG):
  *   LBM_PR_SHIFTED: tau_s = tau, tau_q = (tau - 1/2)/Pr + 1/2, omega = 1/tau_q and the
@@ -89,7 +96,7 @@ extern "C" {
 #define LBM_MEM_HOST 1
 
 typedef struct lbm_params {
-    int lattice;          /* LBM_D2Q37 (D = 2) or LBM_D3Q103 (D = 3)                       */
+    int lattice;          /* LBM_D2Q37, LBM_D2Q33, LBM_D2Q77 (D = 2) or LBM_D3Q103 (D = 3)   */
     double Pr;            /* target Prandtl number, > 0 (Eq. Pr)                          */
     double gamma;         /* if > 0: N_f = 2/(gamma - 1) - D (Eq. Gamma); else N_f is used */
     double N_f;           /* additional degrees of freedom, >= 0, real                     */

@@ -113,9 +113,11 @@ template <int LAT, int ST> struct Launch {
             }
         }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
-        const int sx = c.nx < 4, sy = c.ny < 4, sz = c.nz < 4;
-        // walls on D2Q37 and D3Q103 (reach 3); the create call rejects them for D2Q33
-        constexpr bool W2 = LAT != LAT_D2Q33;
+        // the one-add wrap of x - c is valid for n >= |c|: narrower extents take the modulo
+        constexpr int kWrap = Lattice<LAT>::R > 4 ? Lattice<LAT>::R : 4;
+        const int sx = c.nx < kWrap, sy = c.ny < kWrap, sz = c.nz < kWrap;
+        // walls on D2Q37 and D3Q103 (reach 3); the create call rejects them for D2Q33 and D2Q77
+        constexpr bool W2 = LAT == LAT_D2Q37 || LAT == LAT_D3Q103;
         if (c.kernel == 4) {
             if (W2 && c.walls)
                 k_stream_collide_2p<LAT, ST, W2><<<grid, kTx, 0, st>>>((const T *)src, (T *)dst, kp, sx, sy, sz);
@@ -130,7 +132,7 @@ template <int LAT, int ST> struct Launch {
     }
     static void walls(const Ctx &c, void *buf, cudaStream_t st)
     {
-        if constexpr (LAT != LAT_D2Q33) {
+        if constexpr (LAT == LAT_D2Q37 || LAT == LAT_D3Q103) {
             WallParams wp;
             for (int b = 0; b < 2; ++b) {
                 for (int d = 0; d < 3; ++d) wp.vw[b][d] = (float)(c.wall_u[b][d] / c.r);

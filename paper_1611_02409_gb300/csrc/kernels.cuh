@@ -15,7 +15,8 @@ namespace lbm {
 constexpr int kDiagNV = 10;      // diagnostics partial sums per block
 constexpr int kDiagThreads = 256;
 
-// x - C wrapped into [0, n); `small` grids (n < 4) take the general modulo path.
+// x - C wrapped into [0, n); `small` grids (n < max(4, reach): one add would not reach
+// [0, n)) take the general modulo path.
 template <int C> __device__ __forceinline__ int wrap_sub(int x, int n, bool small)
 {
     int v = x - C;
@@ -104,7 +105,7 @@ __device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop 
     cell_state<LAT, std::is_same<V, f2>::value>(kp, m, c);
     EqState<D, V> e;
     es_state<LAT>(kp, c, e);
-    PolyCoef<D, V> pc;
+    PolyCoef<D, V, Lattice<LAT>::ORDER> pc;
     poly_coeffs<D>(e, kp.r, kp.R2_hi, PRECISE ? kp.R2_lo : 0.f, pc);
     EqScalT<V> z = eq_scalars<D>(e, kp.halfNf);
     z.om1 = 1.f - kp.omega;
@@ -401,7 +402,7 @@ __device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho,
     constexpr int Q = Lattice<LAT>::Q;
     EqState<D> e;
     maxwell_state<D>(drho, v, kp.r, kp.R2_hi, th, e);
-    PolyCoef<D> pc;
+    PolyCoef<D, float, Lattice<LAT>::ORDER> pc;
     poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
     const EqScal z = eq_scalars<D>(e, kp.halfNf);
     s[0] = z.drho + pc.k[0];

@@ -6,6 +6,9 @@
 // (0,0,0), (1,0,0), (1,1,1), (2,0,0), (2,1,0), (2,2,0), (2,2,2), (3,0,0), (3,1,1), (3,3,3).
 // D2Q33: Shim's lattice of Table D2Q33 (Sec. VI B, the shock tube): shells (0,0), (1,0),
 // (1,1), (2,0), (2,2), (3,0), (2,1), (4,4), at its own scale; reach 4.
+// D2Q77: a degree-13 lattice for the sixth-order (Burnett) expansion of Sec. IV, which the
+// paper names but gives no lattice for: shells (0,0), (1,0), (1,1), (2,0), (2,1), (2,2),
+// (3,0), (3,1), (3,2), (3,3), (4,0), (4,1), (4,4), (5,0), (5,3) at its own scale; reach 5.
 //
 // The order is the library's own: index 0 is the rest velocity, then opposite pairs
 // (2k+1, 2k+2) with c_{2k+2} = -c_{2k+1}, so a kernel evaluates the even and odd parts
@@ -19,12 +22,18 @@
 
 namespace lbm {
 
-enum : int { LAT_D2Q37 = 1, LAT_D3Q103 = 2, LAT_D2Q33 = 3 };
+enum : int { LAT_D2Q37 = 1, LAT_D3Q103 = 2, LAT_D2Q33 = 3, LAT_D2Q77 = 4 };
 
 template <int LAT> struct LatticeDims;
 template <> struct LatticeDims<LAT_D2Q37> { static constexpr int D = 2, Q = 37, NSHELL = 8; };
 template <> struct LatticeDims<LAT_D3Q103> { static constexpr int D = 3, Q = 103, NSHELL = 10; };
 template <> struct LatticeDims<LAT_D2Q33> { static constexpr int D = 2, Q = 33, NSHELL = 8; };
+template <> struct LatticeDims<LAT_D2Q77> { static constexpr int D = 2, Q = 77, NSHELL = 15; };
+
+// Order N of the equilibrium's Hermite expansion: 4 (Eq. GExpansion) on the degree-9
+// lattices, 6 (the Burnett order, Sec. IV) on the degree-13 D2Q77.
+template <int LAT> struct LatticeOrder { static constexpr int N = 4; };
+template <> struct LatticeOrder<LAT_D2Q77> { static constexpr int N = 6; };
 
 struct VelTable {
     int c[128][3];
@@ -46,17 +55,22 @@ LBM_HD constexpr VelTable build_table(int lat)
                                  {2, 2, 0}, {2, 2, 2}, {3, 0, 0}, {3, 1, 1}, {3, 3, 3}};
     const int kShells33[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0},
                                  {2, 2, 0}, {3, 0, 0}, {2, 1, 0}, {4, 4, 0}};
+    const int kShells77[15][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0},
+                                  {2, 2, 0}, {3, 0, 0}, {3, 1, 0}, {3, 2, 0}, {3, 3, 0},
+                                  {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 3, 0}};
     const int D = lat == LAT_D3Q103 ? 3 : 2;
     VelTable t{};
     t.Q = 1;
     t.c[0][0] = t.c[0][1] = t.c[0][2] = 0;
     t.shell[0] = 0;
-    const int nsh = D == 2 ? 8 : 10;
+    const int nsh = lat == LAT_D2Q77 ? 15 : (D == 2 ? 8 : 10);
     const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     for (int s = 1; s < nsh; ++s) {
         int gen[3] = {0, 0, 0};
         for (int d = 0; d < 3; ++d)
-            gen[d] = lat == LAT_D2Q33 ? kShells33[s][d] : (D == 2 ? kShells2[s][d] : kShells3[s][d]);
+            gen[d] = lat == LAT_D2Q33   ? kShells33[s][d]
+                     : lat == LAT_D2Q77 ? kShells77[s][d]
+                                        : (D == 2 ? kShells2[s][d] : kShells3[s][d]);
         const int np = D == 2 ? 2 : 6;
         for (int p = 0; p < np; ++p)
             for (int m = 0; m < (1 << D); ++m) {
@@ -93,6 +107,7 @@ template <int LAT> struct Lattice {
     static constexpr int D = LatticeDims<LAT>::D;
     static constexpr int Q = LatticeDims<LAT>::Q;
     static constexpr int NSHELL = LatticeDims<LAT>::NSHELL;
+    static constexpr int ORDER = LatticeOrder<LAT>::N;
     static constexpr VelTable T = build_table(LAT);
     static constexpr int R = max_reach(T);   // largest |c_i| component: the stencil's reach
     static_assert(T.Q == Q, "velocity count");
@@ -101,18 +116,20 @@ template <int LAT> constexpr VelTable Lattice<LAT>::T;
 
 template <int LAT, int I, int DIM> LBM_HD constexpr int cv() { return Lattice<LAT>::T.c[I][DIM]; }
 
-// Monomials c^alpha of total degree <= 4 in D variables, ordered by degree.
+// Monomials c^alpha of total degree <= N in D variables, ordered by degree (and, within a
+// degree, by falling exponent of c_x): the tables for N = 4 and N = 6 share their first
+// entries.  Sized for D = 3, N = 4 (35) and D = 2, N = 6 (28).
 struct MonoTable {
     int e[35][3];
     int deg[35];
     int K;
 };
 
-LBM_HD constexpr MonoTable build_monos(int D)
+LBM_HD constexpr MonoTable build_monos(int D, int N)
 {
     MonoTable m{};
     m.K = 0;
-    for (int n = 0; n <= 4; ++n)
+    for (int n = 0; n <= N; ++n)
         for (int a = n; a >= 0; --a)
             for (int b = n - a; b >= 0; --b) {
                 int c = n - a - b;
@@ -126,11 +143,15 @@ LBM_HD constexpr MonoTable build_monos(int D)
     return m;
 }
 
-template <int D> struct Monos {
-    static constexpr MonoTable M = build_monos(D);
+template <int D, int N = 4> struct Monos {
+    static_assert((D == 2 && N <= 6) || N <= 4, "monomial table size");
+    static constexpr MonoTable M = build_monos(D, N);
     static constexpr int K = M.K;
 };
-template <int D> constexpr MonoTable Monos<D>::M;
+template <int D, int N> constexpr MonoTable Monos<D, N>::M;
+
+// index of the 2-D monomial c_x^i c_y^j in the table
+LBM_HD constexpr int mono_k2(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
 
 LBM_HD constexpr int ipow(int b, int e)
 {
@@ -143,8 +164,9 @@ LBM_HD constexpr int ipow(int b, int e)
 template <int LAT, int I, int K> LBM_HD constexpr int mono_at()
 {
     constexpr int D = Lattice<LAT>::D;
+    using M = Monos<D, Lattice<LAT>::ORDER>;
     int v = 1;
-    for (int d = 0; d < D; ++d) v *= ipow(Lattice<LAT>::T.c[I][d], Monos<D>::M.e[K][d]);
+    for (int d = 0; d < D; ++d) v *= ipow(Lattice<LAT>::T.c[I][d], M::M.e[K][d]);
     return v;
 }
 

@@ -52,11 +52,12 @@ struct lbm_handle {
 
 // The measured-fastest variant for the configuration (GB300, 4096^2 / 256^3 workloads):
 // paired cells for 16-bit storage on the 2-D lattice (even rows), the two-pass kernel for
-// the 3-D lattice (its 206 values per cell do not fit the register file), else direct.
+// the 3-D lattice and D2Q77 (their 206 and 154 values per cell do not fit the register
+// file), else direct.
 static int default_kernel(const lbm_handle *h)
 {
     if (h->ops.paired_ok(h->ctx)) return LBM_KERNEL_PAIRED;
-    if (h->D == 3) return LBM_KERNEL_TWOPASS;
+    if (h->D == 3 || h->p.lattice == LBM_D2Q77) return LBM_KERNEL_TWOPASS;
     return LBM_KERNEL_DIRECT;
 }
 
@@ -133,7 +134,7 @@ struct Mapped {
 // Validation and parameter mapping shared by lbm_create and lbm_map_params.
 static int map_params(const lbm_params &p, Mapped &m)
 {
-    if (p.lattice == LBM_D2Q37 || p.lattice == LBM_D2Q33) m.D = 2;
+    if (p.lattice == LBM_D2Q37 || p.lattice == LBM_D2Q33 || p.lattice == LBM_D2Q77) m.D = 2;
     else if (p.lattice == LBM_D3Q103) m.D = 3;
     else return set_err(nullptr, LBM_ERR_ARG, "unknown lattice");
     const int D = m.D;
@@ -141,7 +142,7 @@ static int map_params(const lbm_params &p, Mapped &m)
     if ((long long)p.nx * p.ny * (D == 3 ? p.nz : 1) > (1LL << 31) - 1)
         return set_err(nullptr, LBM_ERR_ARG, "grid too large");
     if (p.bc_y != LBM_PERIODIC && p.bc_y != LBM_WALLS) return set_err(nullptr, LBM_ERR_ARG, "bad bc_y");
-    if (p.bc_y == LBM_WALLS && (p.lattice == LBM_D2Q33 || p.ny < 5))
+    if (p.bc_y == LBM_WALLS && (p.lattice == LBM_D2Q33 || p.lattice == LBM_D2Q77 || p.ny < 5))
         return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 or D3Q103 and ny >= 5");
     if (p.bc_x != LBM_PERIODIC && p.bc_x != LBM_OPEN) return set_err(nullptr, LBM_ERR_ARG, "bad bc_x");
     if (p.bc_x == LBM_OPEN && D != 2) return set_err(nullptr, LBM_ERR_ARG, "open x ends need D = 2");

@@ -1,0 +1,7 @@
+// Kernel instantiations for one lattice and storage form (one unit each, so the build
+// compiles them in parallel).
+#include "dispatch.cuh"
+
+namespace lbm {
+Ops ops_d2q77_bf16() { return make_ops_st<LAT_D2Q77, ST_BF16>(); }
+} // namespace lbm

@@ -42,12 +42,17 @@ Ops ops_d3q103_bf16();
 Ops ops_d2q33_fp32();
 Ops ops_d2q33_fp16();
 Ops ops_d2q33_bf16();
+Ops ops_d2q77_fp32();
+Ops ops_d2q77_fp16();
+Ops ops_d2q77_bf16();
 
-// The launch table of a lattice (LBM_D2Q37 = 1, LBM_D3Q103 = 2, LBM_D2Q33 = 3) and storage form.
+// The launch table of a lattice (LBM_D2Q37 = 1, LBM_D3Q103 = 2, LBM_D2Q33 = 3, LBM_D2Q77 = 4)
+// and storage form.
 inline Ops ops_for(int lattice, int storage)
 {
     if (lattice == 1) return storage == 1 ? ops_d2q37_fp16() : storage == 2 ? ops_d2q37_bf16() : ops_d2q37_fp32();
     if (lattice == 3) return storage == 1 ? ops_d2q33_fp16() : storage == 2 ? ops_d2q33_bf16() : ops_d2q33_fp32();
+    if (lattice == 4) return storage == 1 ? ops_d2q77_fp16() : storage == 2 ? ops_d2q77_bf16() : ops_d2q77_fp32();
     return storage == 1 ? ops_d3q103_fp16() : storage == 2 ? ops_d3q103_bf16() : ops_d3q103_fp32();
 }
 void launch_diag_final(const double *partials, int nblk, double *out, cudaStream_t st);

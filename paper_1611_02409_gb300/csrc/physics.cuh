@@ -135,9 +135,10 @@ template <int D, class V = float> struct EqState {
     V th_rel;             // T_rel - 1
 };
 
-// Monomial coefficients of q(xi) = P(xi) - 1 at xi = r c, for the state s.
-template <int D, class V = float> struct PolyCoef {
-    static constexpr int K = Monos<D>::K;
+// Monomial coefficients of q(xi) = P(xi) - 1 at xi = r c, for the state s, up to the
+// expansion's order N.
+template <int D, class V = float, int N = 4> struct PolyCoef {
+    static constexpr int K = Monos<D, N>::K;
     V k[K];
 };
 
@@ -156,10 +157,95 @@ __device__ __forceinline__ V c4_of(const V (&A)[D][D], const V (&u)[D], int a, i
          + u[a] * u[b] * u[c] * u[d];
 }
 
-// Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!.
-template <int D, class V>
+// Probabilists' Hermite polynomials He_k(x) = sum_j he_coef(k, j) x^j, from the
+// recurrence He_k = x He_{k-1} - (k - 1) He_{k-2}, He_0 = 1, He_1 = x.
+LBM_HD constexpr int he_coef(int k, int j)
+{
+    if (j < 0 || j > k) return 0;
+    if (k == 0) return 1;
+    if (k == 1) return j == 1 ? 1 : 0;
+    return he_coef(k - 1, j - 1) - (k - 1) * he_coef(k - 2, j);
+}
+
+// Product of homogeneous polynomials in (t_x, t_y), f[a] the coefficient of t_x^a t_y^(n-a).
+template <int NA, int NB, class V>
+__device__ __forceinline__ void hmul(const V (&f)[NA], const V (&g)[NB], V (&out)[NA + NB - 1])
+{
+#pragma unroll
+    for (int a = 0; a < NA + NB - 1; ++a) out[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) out[a + b] = vfma(f[a], g[b], out[a + b]);
+}
+
+// Fifth- and sixth-order terms of the 2-D expansion (Sec. IV: a^(5), a^(6), the Burnett
+// order), added to the monomial coefficients.  With a^(n) . H^(n) / n! written over
+// multi-indices alpha as b_alpha He_alpha(xi), b_alpha is the t^alpha coefficient of the
+// generating function exp(u.t + t.(Lambda - delta).t / 2) of the Gaussian's Hermite
+// coefficients (the same sums over Lambda^beta delta^(alpha-beta) u^(n-2 alpha) products as
+// Eq. fESCoe): with P1 = u.t and P2 = t.A.t / 2, its degree-5 part is
+// P1^5/120 + P1^3 P2/6 + P1 P2^2/2 and its degree-6 part P1^6/720 + P1^4 P2/24 +
+// P1^2 P2^2/4 + P2^3/6.  He_alpha(xi) = He_{a}(xi_x) He_{n-a}(xi_y) then spreads each b_alpha
+// over the monomials of degree n, n-2, ...; xi = r c scales degree m by r^m.
+template <class V>
+__device__ __forceinline__ void burnett_terms(const EqState<2, V> &s, float r, PolyCoef<2, V, 6> &pc)
+{
+    const V p1[2] = {s.u[1], s.u[0]};
+    const V p2[3] = {0.5f * s.A[1][1], s.A[0][1], 0.5f * s.A[0][0]};
+    V p1_2[3], p1_3[4], p1_4[5], p1_5[6], p1_6[7], p2_2[5], p2_3[7];
+    hmul(p1, p1, p1_2);
+    hmul(p1_2, p1, p1_3);
+    hmul(p1_3, p1, p1_4);
+    hmul(p1_4, p1, p1_5);
+    hmul(p1_5, p1, p1_6);
+    hmul(p2, p2, p2_2);
+    hmul(p2_2, p2, p2_3);
+    V t5a[6], t5b[6], t6a[7], t6b[7];
+    hmul(p1_3, p2, t5a);
+    hmul(p1, p2_2, t5b);
+    hmul(p1_4, p2, t6a);
+    hmul(p1_2, p2_2, t6b);
+    V b5[6], b6[7];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) b5[a] = (1.f / 120.f) * p1_5[a] + (1.f / 6.f) * t5a[a] + 0.5f * t5b[a];
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+        b6[a] = (1.f / 720.f) * p1_6[a] + (1.f / 24.f) * t6a[a] + 0.25f * t6b[a] + (1.f / 6.f) * p2_3[a];
+    // monomial xi_x^i xi_y^j: odd degrees from n = 5, even degrees from n = 6
+    float rp[7] = {1.f, r, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int m = 2; m < 7; ++m) rp[m] = rp[m - 1] * r;
+    static_for<0, 7>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        static_for<0, 7 - i>([&](auto JJ) {
+            constexpr int j = decltype(JJ)::value;
+            constexpr int n = (i + j) % 2 ? 5 : 6;
+            if constexpr (i + j <= n) {
+                V acc = 0.f;
+                static_for<0, n + 1>([&](auto AA) {
+                    constexpr int a = decltype(AA)::value;
+                    constexpr int h = he_coef(a, i) * he_coef(n - a, j);
+                    if constexpr (h != 0) {
+                        if constexpr (n == 5) acc = vfma(V((float)h), b5[a], acc);
+                        else acc = vfma(V((float)h), b6[a], acc);
+                    }
+                });
+                constexpr int K = mono_k2(i, j);
+                static_assert(Monos<2, 6>::M.e[K][0] == i && Monos<2, 6>::M.e[K][1] == j, "monomial order");
+                if constexpr (i + j <= 4) pc.k[K] = vfma(s.rho * rp[i + j], acc, pc.k[K]);
+                else pc.k[K] = s.rho * rp[i + j] * acc;
+            }
+        });
+    });
+}
+
+// Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!
+// for the fourth-order expansion (Eq. GExpansion); with N = 6 (2-D) the fifth- and
+// sixth-order terms are added.
+template <int D, class V, int N>
 __device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, float R2_hi, float R2_lo,
-                                            PolyCoef<D, V> &pc)
+                                            PolyCoef<D, V, N> &pc)
 {
     const auto &A = s.A;
     const auto &u = s.u;
@@ -211,7 +297,7 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, flo
                      - 0.5f * rho * (trA * A[a][b] + 2.f * A2[a][b] + trA * u[a] * u[b] + 2.f * Au[a] * u[b]
                                      + 2.f * Au[b] * u[a] + u2 * A[a][b] + u2 * u[a] * u[b]);
     const float r3 = R2_hi * r, r4 = R2_hi * R2_hi;
-    static_for<0, PolyCoef<D>::K>([&](auto KK) {
+    static_for<0, Monos<D>::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
         constexpr int m = Monos<D>::M.deg[K];
         constexpr float inv = (float)inv_alpha_factorial<D, K>();
@@ -229,19 +315,25 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, flo
         else v = r4 * inv * rho * c4_of<D, V>(A, u, i0, i1, i2, i3);
         pc.k[K] = v;
     });
+    if constexpr (N == 6) {
+        static_assert(D == 2, "the sixth-order expansion is built for the 2-D lattice");
+        burnett_terms<V>(s, r, pc);
+    }
 }
 
 // Even and odd parts of q at velocity I (compile-time), q(c_I) = E + O, q(-c_I) = E - O.
 template <int LAT, int I, class V>
-__device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D, V> &pc, V &E, V &O)
+__device__ __forceinline__ void poly_eval_pair(const PolyCoef<Lattice<LAT>::D, V, Lattice<LAT>::ORDER> &pc, V &E,
+                                               V &O)
 {
     constexpr int D = Lattice<LAT>::D;
+    using M = Monos<D, Lattice<LAT>::ORDER>;
     V e = 0.f, o = 0.f;
-    static_for<0, Monos<D>::K>([&](auto KK) {
+    static_for<0, M::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
         constexpr int mv = mono_at<LAT, I, K>();
         if constexpr (mv != 0) {
-            if constexpr (Monos<D>::M.deg[K] % 2 == 0) {
+            if constexpr (M::M.deg[K] % 2 == 0) {
                 if constexpr (mv == 1) e += pc.k[K];
                 else if constexpr (mv == -1) e -= pc.k[K];
                 else e = vfma(V((float)mv), pc.k[K], e);

@@ -15,7 +15,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--lattice", default="d2q37", choices=["d2q37", "d3q103"])
+    ap.add_argument("--lattice", default="d2q37", choices=["d2q37", "d3q103", "d2q33", "d2q77"])
     ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--steps", type=int, default=10)
@@ -29,8 +29,9 @@ def main():
     n = a.grid
     params = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655, storage=a.storage,
                   kernel={"auto": 0, "direct": 1, "staged": 2, "paired": 3, "twopass": 4}[a.kernel])
-    if a.lattice == "d2q37":
-        sim = lbm.Simulation(lattice=lbm.LBM_D2Q37, nx=n, ny=n, **params)
+    if a.lattice in ("d2q37", "d2q33", "d2q77"):
+        lat = {"d2q37": lbm.LBM_D2Q37, "d2q33": lbm.LBM_D2Q33, "d2q77": lbm.LBM_D2Q77}[a.lattice]
+        sim = lbm.Simulation(lattice=lat, nx=n, ny=n, **params)
         fields = inputs.taylor_green_2d(n)
         cells = n * n
     else:

@@ -26,16 +26,21 @@ def test_exports_every_declared_symbol(L):
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103), (3, O.D2Q33)])
+@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103), (3, O.D2Q33), (4, O.D2Q77)])
 def test_library_lattice_matches_oracle(L, lat, olat):
-    # two independent FP64 derivations of the same lattice must agree
+    # two independent FP64 derivations of the same lattice must agree.  D2Q77's degree-12
+    # conditions leave its scale r a root known to ~1e-14 in double precision, and its
+    # smallest weights (2e-7) move by ~1e-13 with it: compared absolutely there.
     D, r, c, w = L.lbm_lattice_table(lat)
     Do, ro, co, wo = O.lattice(olat)
     assert D == Do and len(c) == len(co)
     assert abs(r - ro) < 1e-13
     key = {tuple(v): wt for v, wt in zip(co, wo)}
     for v, wt in zip(c, w):
-        assert wt == pytest.approx(key[tuple(v)], rel=1e-12)
+        if lat == 4:
+            assert abs(wt - key[tuple(v)]) < 2e-13
+        else:
+            assert wt == pytest.approx(key[tuple(v)], rel=1e-12)
     # the library orders opposite velocities in adjacent pairs after the rest velocity
     assert tuple(c[0]) == (0, 0, 0)
     for k in range(1, len(c), 2):
@@ -58,6 +63,7 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
                                  dict(storage=9), dict(pr_mode=4),
                                  dict(kappa=1.0, Pr=0.71), dict(pr_mode=1, Pr=2.0, tau=0.9),
                                  dict(bc_y=1, ny=16, wall_T=[1.0, -1.0]), dict(lattice=3, bc_y=1, ny=16),
+                                 dict(lattice=4, bc_y=1, ny=16),
                                  dict(bc_x=5), dict(lattice=2, bc_x=2)])
 def test_invalid_parameters_rejected_without_gpu(L, bad):
     p = L.make_params(**bad)
