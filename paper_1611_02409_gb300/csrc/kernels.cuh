@@ -303,6 +303,73 @@ template <int ST, int Q> struct RawPop2 {
     }
 };
 
+// Values of the degree-<=4 monomials at each velocity of a 2-D lattice, for the paired
+// kernel's rolled relaxation: one loop body for every opposite pair, the velocity's
+// monomial values read from the constant bank instead of compiled into 18 copies.  The
+// paired kernel is bound by instruction fetch (its unrolled cell is larger than the
+// instruction cache holds for three warps per scheduler at different points); the rolled
+// relaxation executes more instructions (multiplications by 0 and 1, a loop) from a
+// smaller footprint, +2 % (FP16) / +5 % (BF16) at 4096^2.
+template <int LAT> struct MonoVals {
+    float m[Lattice<LAT>::Q][Monos<2>::K];
+};
+template <int LAT> constexpr MonoVals<LAT> make_mono_vals()
+{
+    MonoVals<LAT> v{};
+    for (int i = 0; i < Lattice<LAT>::Q; ++i)
+        for (int k = 0; k < Monos<2>::K; ++k)
+            v.m[i][k] = (float)(ipow(Lattice<LAT>::T.c[i][0], Monos<2>::M.e[k][0]) *
+                                ipow(Lattice<LAT>::T.c[i][1], Monos<2>::M.e[k][1]));
+    return v;
+}
+static __constant__ MonoVals<LAT_D2Q37> c_mono_d2q37 = make_mono_vals<LAT_D2Q37>();
+
+// The paired cells' collision (packed FP32 lanes, the non-compensated sums of 16-bit
+// storage): the moment sums read the gathered words from registers (unrolled), the
+// relaxation, a rolled loop over opposite pairs, from their shared-memory column (word I
+// at col[I * 128]).  Per lane the arithmetic and its order are collide_store's.
+template <int LAT, int ST>
+__device__ __forceinline__ void collide_store_paired(const KParams<LAT> &kp, uint32_t (&rs)[Lattice<LAT>::Q],
+                                                     uint32_t (&rt)[Lattice<LAT>::Q], const uint32_t *col,
+                                                     typename Storage<ST>::T *__restrict__ dst, long long o)
+{
+    static_assert(LAT == LAT_D2Q37, "rolled relaxation: D2Q37 monomial table");
+    constexpr int D = 2;
+    constexpr int Q = Lattice<LAT>::Q;
+    using V = f2;
+    RawMoments<D, V> m;
+    raw_moments<LAT, false>(kp, RawPop2<ST, Q>{rs, rt}, m);
+    CellState<D, V> c;
+    cell_state<LAT, true>(kp, m, c);
+    EqState<D, V> e;
+    es_state<LAT>(kp, c, e);
+    PolyCoef<D, V, 4> pc;
+    poly_coeffs<D>(e, kp.r, kp.R2_hi, 0.f, pc);
+    EqScalT<V> z = eq_scalars<D>(e, kp.halfNf);
+    z.om1 = 1.f - kp.omega;
+    z.wdrho = kp.omega * z.drho;
+    z.whb = kp.omega * z.hb;
+    z.whr = kp.omega * z.hr;
+    typename Storage<ST>::T *cell = dst + o;
+    const TableOff so{kp.soff};
+    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], Storage<ST>::cvt2(col[0]),
+                         Storage<ST>::cvt2(col[Q * 128]));
+#pragma unroll 1
+    for (int I = 1; I < Q; I += 2) {
+        V E = 0.f, O = 0.f;
+        static_for<0, Monos<2>::K>([&](auto KK) {
+            constexpr int K = decltype(KK)::value;
+            const float mv = c_mono_d2q37.m[I][K];
+            if constexpr (Monos<2>::M.deg[K] % 2 == 0) E = vfma(V(mv), pc.k[K], E);
+            else O = vfma(V(mv), pc.k[K], O);
+        });
+        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, Storage<ST>::cvt2(col[I * 128]),
+                             Storage<ST>::cvt2(col[(Q + I) * 128]));
+        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, Storage<ST>::cvt2(col[(I + 1) * 128]),
+                             Storage<ST>::cvt2(col[(Q + I + 1) * 128]));
+    }
+}
+
 // 32-bit word of the 16-bit values at element offsets e and e + 1 from p, for an odd e:
 // the two aligned words around them, then a byte permute.
 __device__ __forceinline__ uint32_t ld_pair_odd(const char *p)
@@ -390,7 +457,15 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
             rt[I] |= xt[I] << 16;
         });
     }
-    collide_store<LAT, ST>(kp, RawPop2<ST, Q>{rs, rt}, dst, o);
+    // the words also go to this thread's shared-memory column for the rolled relaxation
+    __shared__ uint32_t park[2 * Q * 128];
+    uint32_t *col = park + threadIdx.x;
+    static_for<0, Q>([&](auto II) {
+        constexpr int I = decltype(II)::value;
+        col[I * 128] = rs[I];
+        col[(Q + I) * 128] = rt[I];
+    });
+    collide_store_paired<LAT, ST>(kp, rs, rt, col, dst, o);
 }
 
 // Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].
