@@ -45,11 +45,38 @@ def workload(storage):
             f"(N_f=3), kappa=0.2, tau=0.528655 (nu=0.02 lu), U0=0.02, T amplitude 0.01")
 
 
+def code_only(src):
+    """C++ source without comments and with whitespace runs collapsed (string and character
+    literals kept), so that a comment edit leaves the kernel hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_src_sha():
+    """Hash of the kernel sources' code (comments and layout excluded): the key under which
+    ncu traffic counters taken on that code stay valid."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1611_02409_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1611_02409_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    // a cell away from every periodic seam (|c| <= 3) gathers at fixed byte offsets; only
-    // the warps holding the first and last three cells of a row diverge
+    // a cell at least the stencil's reach R away from every periodic seam or open end
+    // gathers at fixed byte offsets; only the warps holding the first and last R cells of
+    // a row diverge
     constexpr int R = Lattice<LAT>::R;
     bool interior = x >= R && x + R < kp.nx;
     if constexpr (!WALLS) interior = interior && y >= R && y + R < kp.ny;
@@ -194,7 +195,8 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
 }
 
 // Populations read from the source buffer where they are used (two-pass kernel): a cell's
-// wrapped source columns, rows and planes for the displacements -3..3 are tabulated once.
+// wrapped source columns, rows and planes for the displacements -R..R (R the stencil's
+// reach) are tabulated once.
 // Opposite pairs are read in chunks of CH pairs: prefetch<P>() at the first pair of a
 // chunk issues the chunk's 4 CH loads (g and h of both members) into registers before any
 // of them is used, so each warp keeps a chunk of loads in flight; sv<I>() / tv<I>() then
