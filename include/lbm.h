@@ -82,14 +82,18 @@ extern "C" {
 #define LBM_OPEN 2
 
 /* stream-collide kernel variants (lbm_set_kernel / lbm_autotune) */
-#define LBM_KERNEL_AUTO 0    /* the library's default for the configuration            */
+#define LBM_KERNEL_AUTO 0    /* the library's default for the configuration: PAIRED
+                                where admissible, TWOPASS on D3Q103 and D2Q77, else
+                                DIRECT                                                 */
 #define LBM_KERNEL_DIRECT 1  /* one cell per thread, populations gathered from HBM     */
 #define LBM_KERNEL_STAGED 2  /* persistent tiles staged in shared memory by bulk
-                                asynchronous copies (D = 2, nx a multiple of 128)      */
+                                asynchronous copies (D2Q37, periodic x, nx a multiple
+                                of the tile width: 128 cells)                          */
 #define LBM_KERNEL_PAIRED 3  /* two neighbouring cells per thread in packed FP32 pairs
-                                (D = 2, FP16 or BF16 storage, nx even)                 */
+                                (D2Q37, FP16 or BF16 storage, periodic x, nx even)     */
 #define LBM_KERNEL_TWOPASS 4 /* one cell per thread, populations read twice (moments,
-                                then relaxation) instead of held in registers          */
+                                then relaxation) instead of held in registers; every
+                                lattice                                                */
 
 /* memory space of field pointers */
 #define LBM_MEM_DEVICE 0
