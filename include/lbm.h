@@ -198,6 +198,18 @@ int lbm_autotune(lbm_handle *h, int steps, int *chosen);
  * operation (re-initialise the fields).  Other kernels ignore it.  Synchronises. */
 int lbm_debug_inject_stall(lbm_handle *h, int on);
 
+/* Host-side audit of the stream-collide kernels' addressing (tests only; no device work,
+ * no paper counterpart).  For the configuration *p and kernel variant (LBM_KERNEL_DIRECT,
+ * LBM_KERNEL_PAIRED or LBM_KERNEL_TWOPASS), forms every element index the variant gathers
+ * from and stores to, for every computed cell, with the kernels' own index helpers and
+ * the launch's wrap threshold, and counts the accesses outside the 2 Q planes of a
+ * population buffer (and the 32-bit accesses of the paired kernel off a 4-byte boundary).
+ * wrap_threshold > 0 replaces the launch's threshold (extents below it take the modulo
+ * wrap) so a test can show that a wrong one is caught; 0 keeps the launch's.  Returns the
+ * count (0: every access in bounds), or minus an LBM status for invalid parameters or a
+ * variant the configuration does not admit. */
+long long lbm_debug_index_audit(const lbm_params *p, int variant, int wrap_threshold);
+
 /* Conservation totals of caller-owned FP64 device fields, allocating nothing (the paper
  * has no counterpart: this serves callers that cannot call cudaMalloc, for instance code
  * whose device memory was all reserved up front by a host framework, or a time-critical

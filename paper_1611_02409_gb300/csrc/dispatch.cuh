@@ -113,8 +113,7 @@ template <int LAT, int ST> struct Launch {
             }
         }
         const dim3 grid = rows_grid(c, kp.ny_comp, kTx);
-        // the one-add wrap of x - c is valid for n >= |c|: narrower extents take the modulo
-        constexpr int kWrap = Lattice<LAT>::R > 4 ? Lattice<LAT>::R : 4;
+        constexpr int kWrap = wrap_threshold<LAT>();
         const int sx = c.nx < kWrap, sy = c.ny < kWrap, sz = c.nz < kWrap;
         // walls on D2Q37 and D3Q103 (reach 3); the create call rejects them for D2Q33 and D2Q77
         constexpr bool W2 = LAT == LAT_D2Q37 || LAT == LAT_D3Q103;

@@ -17,7 +17,7 @@ constexpr int kDiagThreads = 256;
 
 // x - C wrapped into [0, n); `small` grids (n < max(4, reach): one add would not reach
 // [0, n)) take the general modulo path.
-template <int C> __device__ __forceinline__ int wrap_sub(int x, int n, bool small)
+template <int C> LBM_HD __forceinline__ int wrap_sub(int x, int n, bool small)
 {
     int v = x - C;
     if (small) return ((v % n) + n) % n;
@@ -31,7 +31,7 @@ template <int C> __device__ __forceinline__ int wrap_sub(int x, int n, bool smal
 
 // Source column x - C of the gather: wrapped (periodic) or, with open ends, clamped to the
 // domain (zero gradient: a population from beyond an end is the end cell's own).
-template <int C> __device__ __forceinline__ int src_x(int x, int n, bool small, bool open)
+template <int C> LBM_HD __forceinline__ int src_x(int x, int n, bool small, bool open)
 {
     if (open) {
         const int v = x - C;
@@ -41,7 +41,7 @@ template <int C> __device__ __forceinline__ int src_x(int x, int n, bool small, 
 }
 
 template <int LAT>
-__device__ __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, int ys, int z)
+LBM_HD __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, int ys, int z)
 {
     return ((long long)z * kp.nys + ys) * kp.nx + x;
 }

@@ -150,6 +150,10 @@ template <int D, int N = 4> struct Monos {
 };
 template <int D, int N> constexpr MonoTable Monos<D, N>::M;
 
+// Extents below this take the modulo wrap of x - c: one add or subtract reaches [0, n)
+// only for n >= |c|, and |c| <= R.
+template <int LAT> LBM_HD constexpr int wrap_threshold() { return Lattice<LAT>::R > 4 ? Lattice<LAT>::R : 4; }
+
 // index of the 2-D monomial c_x^i c_y^j in the table
 LBM_HD constexpr int mono_k2(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
 
@@ -191,7 +195,7 @@ template <int D, int K> LBM_HD constexpr double inv_alpha_factorial()
 }
 
 // Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1.
-template <int B, int E, typename F> __device__ __forceinline__ void static_for(F &&f)
+template <int B, int E, typename F> LBM_HD __forceinline__ void static_for(F &&f)
 {
     if constexpr (B < E) {
         f(std::integral_constant<int, B>{});

@@ -104,6 +104,8 @@ def lib():
             L.lbm_last_error.restype = C.c_char_p
             L.lbm_lattice_info.argtypes = [vp, ip, ip, dp, ip, dp]
             L.lbm_lattice_table.argtypes = [C.c_int, ip, ip, dp, ip, dp]
+            L.lbm_debug_index_audit.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_int]
+            L.lbm_debug_index_audit.restype = C.c_longlong
             L.lbm_map_params.argtypes = [C.POINTER(lbm_params), dp]
             L.lbm_coefficients.argtypes = [vp, dp]
             L.lbm_init_fields.argtypes = [vp, vp, vp, vp, C.c_int]
@@ -158,6 +160,15 @@ def lbm_lattice_table(lattice=LBM_D2Q37):
     _check(lib().lbm_lattice_table(lattice, C.byref(D), C.byref(Q), C.byref(r),
                                    c.ctypes.data_as(C.POINTER(C.c_int)), w.ctypes.data_as(C.POINTER(C.c_double))))
     return D.value, r.value, c[:Q.value].copy(), w[:Q.value].copy()
+
+
+def lbm_debug_index_audit(p: lbm_params, variant: int, wrap_threshold: int = 0) -> int:
+    """Out-of-range (or misaligned) accesses of a kernel variant's addressing for the
+    configuration p, audited on the host (no GPU needed); raises on invalid arguments."""
+    n = lib().lbm_debug_index_audit(C.byref(p), int(variant), int(wrap_threshold))
+    if n < 0:
+        raise LbmError(int(-n), "index audit: invalid configuration or variant")
+    return n
 
 
 def lbm_map_params(p: lbm_params) -> dict:
