@@ -10,7 +10,8 @@
 // is off a 4-byte boundary, or when it is not the element the pull-stream definition
 // names: population i of the cell at (x, y, z) - c_i, periodic by plain modulo, clamped at
 // open x ends, in the ghost rows beyond walls (and the cell's own element for a store).
-// No device work.
+// With walls, the wall kernel's reads (first fluid row, the leaving populations' cells)
+// and writes (wall and ghost rows) are audited too.  No device work.
 #include "../../include/lbm.h"
 #include "dispatch.cuh"
 
@@ -56,8 +57,8 @@ long long want_src(const KParams<LAT> &kp, int set, int i, int x, int y, int z)
     return (long long)(set * Q + i) * kp.plane + ((long long)zs * kp.nys + ys) * kp.nx + xs;
 }
 
-// ... and the element a store of population p of the cell writes: its own.
-template <int LAT> long long want_dst(const KParams<LAT> &kp, int p, int x, int y, int z)
+// ... and the element of population p of the cell (x, y, z) itself (stores, own-cell reads).
+template <int LAT> long long own_elem(const KParams<LAT> &kp, int p, int x, int y, int z)
 {
     return (long long)p * kp.plane + ((long long)z * kp.nys + y + kp.gh) * kp.nx + x;
 }
@@ -85,7 +86,7 @@ void audit_direct(const KParams<LAT> &kp, long long elem, bool sx, bool sy, bool
             t.check((long long)(Q + I) * kp.plane + idx, want_src(kp, 1, I, x, y, z));
         });
     }
-    for (int p = 0; p < 2 * Q; ++p) t.check(o + kp.soff[p] / elem, want_dst(kp, p, x, y, z));
+    for (int p = 0; p < 2 * Q; ++p) t.check(o + kp.soff[p] / elem, own_elem(kp, p, x, y, z));
 }
 
 // k_stream_collide_2p (two-pass): tabulated wrapped columns, rows and planes for -R..R.
@@ -108,7 +109,7 @@ void audit_twopass(const KParams<LAT> &kp, long long elem, bool sx, bool sy, boo
         t.check((long long)(Q + I) * kp.plane + at, want_src(kp, 1, I, x, y, z));
     });
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    for (int p = 0; p < 2 * Q; ++p) t.check(o + kp.soff[p] / elem, want_dst(kp, p, x, y, z));
+    for (int p = 0; p < 2 * Q; ++p) t.check(o + kp.soff[p] / elem, own_elem(kp, p, x, y, z));
 }
 
 // k_stream_collide_pair (two cells x, x + 1 per thread, 16-bit storage, 128-thread blocks).
@@ -154,7 +155,41 @@ void audit_paired(const KParams<LAT> &kp, long long elem, bool sy, int x, int y,
     }
     for (int p = 0; p < 2 * Q; ++p) {
         t.check_word(o + kp.soff[p] / elem);
-        t.check(o + kp.soff[p] / elem, want_dst(kp, p, x, y, 0));
+        t.check(o + kp.soff[p] / elem, own_elem(kp, p, x, y, 0));
+    }
+}
+
+// k_walls (one thread per column x, wall b, plane z): reads the first fluid row's cell and,
+// for each population leaving the fluid toward the wall, the cells 1 .. |c_y| rows inside
+// displaced by -c_x (-c_z); writes the wall row and the two ghost rows beyond it.
+template <int LAT> void audit_walls(const KParams<LAT> &kp, int x, int b, int z, Tally &t)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int n = b == 0 ? 1 : -1;
+    const int yw = b == 0 ? 0 : kp.ny - 1;
+    const int small_x = kp.nx < 4, small_z = kp.nz < 4;   // the wall kernel's own (reach 3)
+    const long long o1 = cell_index<LAT>(kp, x, yw + n + kp.gh, z);
+    for (int p = 0; p < 2 * Q; ++p) t.check((long long)p * kp.plane + o1, own_elem(kp, p, x, yw + n, z));
+    static_for<0, Q>([&](auto II) {
+        constexpr int I = decltype(II)::value;
+        constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
+        const int cn = cy * n;
+        if (cy != 0 && cn < 0) {
+            const int xs = wrap_sub<cx>(x, kp.nx, small_x);
+            const int zs = D == 3 ? wrap_sub<cz>(z, kp.nz, small_z) : 0;
+            for (int sdist = 1; sdist <= -cn; ++sdist) {
+                const int yf = yw + n * sdist;   // a fluid row
+                if (yf < 1 || yf > kp.ny - 2) ++t.bad;
+                const long long want = (long long)I * kp.plane +
+                    (((long long)(D == 3 ? mod(z - cz, kp.nz) : 0) * kp.nys + yf + kp.gh) * kp.nx + mod(x - cx, kp.nx));
+                t.check((long long)I * kp.plane + cell_index<LAT>(kp, xs, yf + kp.gh, zs), want);
+            }
+        }
+    });
+    for (int k = 0; k <= 2; ++k) {
+        const int yr = yw - n * k;            // the wall row, then the ghost rows beyond it
+        const long long o = cell_index<LAT>(kp, x, yr + kp.gh, z);
+        for (int p = 0; p < 2 * Q; ++p) t.check((long long)p * kp.plane + o, own_elem(kp, p, x, yr, z));
     }
 }
 
@@ -177,6 +212,11 @@ template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wr
                 else if constexpr (LAT == LAT_D2Q37)
                     if (x % 2 == 0) audit_paired<LAT, WALLS>(kp, elem, c.ny < 4, x, y, t);
             }
+    // the wall kernel runs after every step whichever variant streamed
+    if constexpr (WALLS)
+        for (int z = 0; z < (D == 3 ? c.nz : 1); ++z)
+            for (int b = 0; b < 2; ++b)
+                for (int x = 0; x < c.nx; ++x) audit_walls<LAT>(kp, x, b, z, t);
     return t.bad;
 }
 
