@@ -246,9 +246,11 @@ int lbm_set_populations(lbm_handle *h, const double *g, const double *hh, int me
  * --------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
-/* n >= 1 parameter sets (lattice LBM_D2Q37, storage LBM_FP32 for every one); every
- * instance starts at the rest state.  Returns LBM_OK or an error (text in
- * lbm_last_error(NULL)). */
+/* n >= 1 parameter sets (lattice LBM_D2Q37, storage LBM_FP32, periodic x for every one;
+ * each instance's 2 Q population planes below 2^31 values, i.e. at most 29,020,049 cells
+ * per plane, nx (ny + 4) with walls and nx ny without: LBM_ERR_ARG otherwise, checked
+ * before any device work); every instance starts at the rest state.  Returns LBM_OK or an
+ * error (text in lbm_last_error(NULL)). */
 int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out);
 int lbm_batch_destroy(lbm_batch *b);
 

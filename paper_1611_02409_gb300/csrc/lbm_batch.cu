@@ -340,6 +340,12 @@ int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out)
             return rc;
         }
         Ctx &c = b->ctx[i];
+        // the step kernel forms an instance's element offsets (p * plane + cell, p < 2 Q) in
+        // 32-bit integers
+        if ((long long)2 * Q * c.plane >= (1LL << 31)) {
+            delete b;
+            return set_global_error(LBM_ERR_ARG, "a batched instance's 2 Q planes must hold fewer than 2^31 values");
+        }
         kps[i] = make_kparams<LAT>(c);
         Inst &in = b->inst0[i];
         memset(&in, 0, sizeof(in));

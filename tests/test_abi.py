@@ -75,3 +75,14 @@ def test_invalid_parameters_rejected_without_gpu(L, bad):
     assert L.lib().lbm_create(C.byref(p), None, C.byref(h)) == L.LBM_ERR_ARG
     assert not h.value
     assert L.lbm_last_error()
+
+
+@pytest.mark.parametrize("nx,ny,walls", [(6000, 6000, 0), (2, 14510025, 0), (1, 29020046, 1)])
+def test_batch_rejects_instances_beyond_32bit_offsets(L, nx, ny, walls):
+    # the batched step forms p * plane + cell (p < 74) in 32-bit integers: an instance
+    # whose 74 planes reach 2^31 values (plane > 29,020,049 cells) is refused at creation,
+    # before any device work
+    p = L.make_params(nx=nx, ny=ny, bc_y=walls, tau=0.8)
+    h = C.c_void_p()
+    assert L.lib().lbm_batch_create(1, C.byref(p), C.byref(h)) == L.LBM_ERR_ARG
+    assert b"2^31" in L.lib().lbm_last_error(None)
