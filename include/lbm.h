@@ -108,7 +108,8 @@ typedef struct lbm_params {
     double tau;           /* tau_f = tau / dt in lattice steps, > 1/2                      */
     int pr_mode;          /* LBM_PR_SHIFTED or LBM_PR_LITERAL                              */
     int storage;          /* LBM_FP32, LBM_FP16 or LBM_BF16                                */
-    int nx, ny, nz;       /* grid; nz = 1 for D = 2; nx, ny >= 1 (walls: ny >= 5)          */
+    int nx, ny, nz;       /* grid; nz = 1 for D = 2; nx, ny >= 1 (walls: ny >= 5);
+                             ny (+ 4 with walls) and nz at most 65535                        */
     int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D2Q37, D3Q103; walls are the planes
                              y = 0 and y = ny - 1, z periodic)                            */
     double wall_u[2][3];  /* bottom (y = 0) / top (y = ny-1) wall velocity (tangential x)   */

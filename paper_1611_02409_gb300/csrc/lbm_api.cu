@@ -141,6 +141,10 @@ static int map_params(const lbm_params &p, Mapped &m)
     if (p.nx < 1 || p.ny < 1 || (D == 3 && p.nz < 1)) return set_err(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
     if ((long long)p.nx * p.ny * (D == 3 ? p.nz : 1) > (1LL << 31) - 1)
         return set_err(nullptr, LBM_ERR_ARG, "grid too large");
+    // the kernels launch one block row per stored row (gridDim.y, walls add four ghost
+    // rows) and one block layer per plane (gridDim.z), each at most 65535
+    if (p.ny + (p.bc_y == LBM_WALLS ? 4 : 0) > 65535 || (D == 3 && p.nz > 65535))
+        return set_err(nullptr, LBM_ERR_ARG, "ny (plus 4 ghost rows with walls) and nz must not exceed 65535");
     if (p.bc_y != LBM_PERIODIC && p.bc_y != LBM_WALLS) return set_err(nullptr, LBM_ERR_ARG, "bad bc_y");
     if (p.bc_y == LBM_WALLS && (p.lattice == LBM_D2Q33 || p.lattice == LBM_D2Q77 || p.ny < 5))
         return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 or D3Q103 and ny >= 5");

@@ -64,7 +64,9 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
                                  dict(kappa=1.0, Pr=0.71), dict(pr_mode=1, Pr=2.0, tau=0.9),
                                  dict(bc_y=1, ny=16, wall_T=[1.0, -1.0]), dict(lattice=3, bc_y=1, ny=16),
                                  dict(lattice=4, bc_y=1, ny=16),
-                                 dict(bc_x=5), dict(lattice=2, bc_x=2)])
+                                 dict(bc_x=5), dict(lattice=2, bc_x=2),
+                                 dict(nx=4, ny=65536), dict(nx=4, ny=65532, bc_y=1),
+                                 dict(lattice=2, nx=4, ny=4, nz=65536)])
 def test_invalid_parameters_rejected_without_gpu(L, bad):
     p = L.make_params(**bad)
     with pytest.raises(L.LbmError) as e:
@@ -77,7 +79,7 @@ def test_invalid_parameters_rejected_without_gpu(L, bad):
     assert L.lbm_last_error()
 
 
-@pytest.mark.parametrize("nx,ny,walls", [(6000, 6000, 0), (2, 14510025, 0), (1, 29020046, 1)])
+@pytest.mark.parametrize("nx,ny,walls", [(6000, 6000, 0), (450, 64489, 0), (450, 64485, 1)])
 def test_batch_rejects_instances_beyond_32bit_offsets(L, nx, ny, walls):
     # the batched step forms p * plane + cell (p < 74) in 32-bit integers: an instance
     # whose 74 planes reach 2^31 values (plane > 29,020,049 cells) is refused at creation,
