@@ -263,10 +263,12 @@ int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const doub
                               const double *Pi, const double *q, int mem);
 
 /* Advances every active instance until all have converged (residual < tol at a check,
- * checks every `check_every` steps) or `max_steps` steps have been taken by the batch.
- * An instance whose fields turn non-finite stops at its next check with residual NaN
- * (lbm_batch_status); the others carry on.  Synchronises.  *steps_taken (may be NULL)
- * receives the number of batch steps run. */
+ * checks every `check_every` steps, 1 <= check_every <= 100000: one window is captured as
+ * a CUDA graph) or `max_steps` steps have been taken by the batch, in whole windows (the
+ * last may run past max_steps by up to check_every - 1 steps).  An instance whose fields
+ * turn non-finite stops at its next check with residual NaN (lbm_batch_status); the
+ * others carry on.  Synchronises.  *steps_taken (may be NULL) receives the number of
+ * batch steps run. */
 int lbm_batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken);
 
 /* Per-instance status (host arrays of n entries, any may be NULL): steps taken, last
@@ -283,8 +285,9 @@ int lbm_batch_activate(lbm_batch *b, int i);
 int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u, double *T, double *Pi, double *q, int mem);
 
 /* Times the step kernel's tile sizes (128, 256 or 512 cells per work item) over
- * `steps` steps on the current state and keeps the fastest; *chosen receives the tile.
- * Resets every instance to the rest state (call before lbm_batch_init_fields). */
+ * `steps` steps (1 <= steps <= 100000, one captured window) on the current state and
+ * keeps the fastest; *chosen receives the tile.  Resets every instance to the rest state
+ * (call before lbm_batch_init_fields). */
 int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen);
 
 /* ---------------------------------------------------------------------------------

@@ -459,7 +459,9 @@ int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const doub
 
 static int batch_run(lbm_batch *b, int max_steps, double tol, int check_every, int *steps_taken)
 {
-    if (!b || max_steps < 0 || check_every < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    // a window of check_every steps is captured as one CUDA graph (two nodes per step)
+    if (!b || max_steps < 0 || check_every < 1 || check_every > 100000)
+        return bfail(b, LBM_ERR_ARG, "need max_steps >= 0 and 1 <= check_every <= 100000");
     int rc = ensure_graph(b, check_every, tol, b->tile);
     if (rc) return rc;
     int done = 0;
@@ -544,7 +546,7 @@ int lbm_batch_moments(lbm_batch *b, int i, double *rho, double *u, double *T, do
 
 int lbm_batch_autotune(lbm_batch *b, int steps, int *chosen)
 {
-    if (!b || steps < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    if (!b || steps < 1 || steps > 100000) return bfail(b, LBM_ERR_ARG, "need 1 <= steps <= 100000");
     cudaEvent_t e0, e1;
     LBM_BCK(b, cudaEventCreate(&e0));
     LBM_BCK(b, cudaEventCreate(&e1));
