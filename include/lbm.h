@@ -201,8 +201,9 @@ int lbm_debug_inject_stall(lbm_handle *h, int on);
 
 /* Host-side audit of the stream-collide kernels' addressing (tests only; no device work,
  * no paper counterpart).  For the configuration *p and kernel variant (LBM_KERNEL_DIRECT,
- * LBM_KERNEL_PAIRED or LBM_KERNEL_TWOPASS), forms every element index the variant gathers
- * from and stores to, for every computed cell, with the kernels' own index helpers and
+ * LBM_KERNEL_PAIRED, LBM_KERNEL_TWOPASS or LBM_AUDIT_BATCH), forms every element index
+ * the variant gathers from and stores to (and, with walls, those of the wall kernel),
+ * for every computed cell, with the kernels' own index helpers and
  * the launch's wrap threshold, and counts the accesses outside the 2 Q planes of a
  * population buffer (and the 32-bit accesses of the paired kernel off a 4-byte boundary).
  * wrap_threshold > 0 replaces the launch's threshold (extents below it take the modulo
@@ -210,6 +211,9 @@ int lbm_debug_inject_stall(lbm_handle *h, int on);
  * count (0: every access in bounds), or minus an LBM status for invalid parameters or a
  * variant the configuration does not admit. */
 long long lbm_debug_index_audit(const lbm_params *p, int variant, int wrap_threshold);
+/* variant value for lbm_debug_index_audit: the batched step's addressing for one instance
+ * (D2Q37, FP32, periodic x; also checks that its 32-bit offsets do not overflow) */
+#define LBM_AUDIT_BATCH 5
 
 /* Conservation totals of caller-owned FP64 device fields, allocating nothing (the paper
  * has no counterpart: this serves callers that cannot call cudaMalloc, for instance code

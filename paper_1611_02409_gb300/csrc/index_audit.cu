@@ -11,7 +11,8 @@
 // names: population i of the cell at (x, y, z) - c_i, periodic by plain modulo, clamped at
 // open x ends, in the ghost rows beyond walls (and the cell's own element for a store).
 // With walls, the wall kernel's reads (first fluid row, the leaving populations' cells)
-// and writes (wall and ghost rows) are audited too.  No device work.
+// and writes (wall and ghost rows) are audited too; LBM_AUDIT_BATCH audits one instance
+// of the batched step (32-bit offsets).  No device work.
 #include "../../include/lbm.h"
 #include "dispatch.cuh"
 
@@ -193,6 +194,40 @@ template <int LAT> void audit_walls(const KParams<LAT> &kp, int x, int b, int z,
     }
 }
 
+// k_bstep (batched instances, D2Q37 FP32): per instance, 32-bit element offsets from the
+// instance's buffer, stencil rows and columns tabulated for -3..3 with the batch's own
+// wrap threshold (4); every product and sum must also fit a 32-bit int.
+void audit_batch(const KParams<LAT_D2Q37> &kp, int walls, int x, int y, Tally &t)
+{
+    constexpr int LAT = LAT_D2Q37, Q = Lattice<LAT>::Q;
+    const long long kMax = 2147483647LL;
+    const int nx = kp.nx, ny = kp.ny, gh = kp.gh;
+    const long long pl = kp.plane;
+    if (pl > kMax) ++t.bad;
+    const bool sx = nx < 4, sy = ny < 4;
+    long long rowo[7], col[7];
+    static_for<0, 7>([&](auto KK) {
+        constexpr int C = decltype(KK)::value - 3;
+        const int ys = walls ? y - C + gh : wrap_sub<C>(y, ny, sy);
+        rowo[KK] = (long long)ys * nx;
+        col[KK] = wrap_sub<C>(x, nx, sx);
+    });
+    static_for<0, Q>([&](auto II) {
+        constexpr int I = decltype(II)::value;
+        const long long idx = rowo[cv<LAT, I, 1>() + 3] + col[cv<LAT, I, 0>() + 3];
+        for (int set = 0; set < 2; ++set) {
+            const long long e = (long long)(set * Q + I) * pl + idx;
+            if (e > kMax || (long long)(set * Q + I) * pl > kMax) ++t.bad;
+            t.check(e, want_src(kp, set, I, x, y, 0));
+        }
+    });
+    const long long o = (long long)(y + gh) * nx + x;
+    for (int p = 0; p < 2 * Q; ++p) {
+        if ((long long)p * pl > kMax) ++t.bad;
+        t.check((long long)p * pl + o, own_elem(kp, p, x, y, 0));
+    }
+}
+
 template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wrap)
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
@@ -207,7 +242,9 @@ template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wr
         for (int yy = 0; yy < ncomp; ++yy)
             for (int x = 0; x < c.nx; ++x) {
                 const int y = y0 + yy;
-                if (variant == LBM_KERNEL_TWOPASS) audit_twopass<LAT, WALLS>(kp, elem, sx, sy, sz, x, y, z, t);
+                if (variant == LBM_AUDIT_BATCH) {
+                    if constexpr (LAT == LAT_D2Q37) audit_batch(kp, c.walls, x, y, t);
+                } else if (variant == LBM_KERNEL_TWOPASS) audit_twopass<LAT, WALLS>(kp, elem, sx, sy, sz, x, y, z, t);
                 else if (variant == LBM_KERNEL_DIRECT) audit_direct<LAT, WALLS>(kp, elem, sx, sy, sz, x, y, z, t);
                 else if constexpr (LAT == LAT_D2Q37)
                     if (x % 2 == 0) audit_paired<LAT, WALLS>(kp, elem, c.ny < 4, x, y, t);
@@ -241,7 +278,11 @@ extern "C" long long lbm_debug_index_audit(const lbm_params *p, int variant, int
     if (rc != LBM_OK && rc != LBM_WARN_PR_RANGE) return -rc;
     const bool d2q37_16 = p->lattice == LBM_D2Q37 && p->storage != LBM_FP32;
     if (variant == LBM_KERNEL_PAIRED && !(d2q37_16 && !c.open_x && c.nx % 2 == 0)) return -LBM_ERR_ARG;
-    if (variant != LBM_KERNEL_DIRECT && variant != LBM_KERNEL_TWOPASS && variant != LBM_KERNEL_PAIRED)
+    if (variant == LBM_AUDIT_BATCH &&
+        !(p->lattice == LBM_D2Q37 && p->storage == LBM_FP32 && !c.open_x && 2LL * Q * c.plane < (1LL << 31)))
+        return -LBM_ERR_ARG;   // what lbm_batch_create admits
+    if (variant != LBM_KERNEL_DIRECT && variant != LBM_KERNEL_TWOPASS && variant != LBM_KERNEL_PAIRED &&
+        variant != LBM_AUDIT_BATCH)
         return -LBM_ERR_ARG;
     if (wrap_threshold < 0) return -LBM_ERR_ARG;
     switch (p->lattice) {

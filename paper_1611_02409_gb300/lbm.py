@@ -29,6 +29,7 @@ LBM_D2Q37 = 1
 LBM_D3Q103 = 2
 LBM_D2Q33 = 3
 LBM_D2Q77 = 4
+LBM_AUDIT_BATCH = 5
 LBM_PR_SHIFTED = 0
 LBM_PR_LITERAL = 1
 LBM_FP32 = 0

@@ -52,6 +52,18 @@ def test_3d(audit, walls):
             assert audit(L.LBM_D3Q103, "fp32", walls, False, nx, ny, nz, v) == 0, (nx, ny, nz, v)
 
 
+def test_batched_step(audit):
+    # one instance of the batched step (D2Q37, FP32): same definition, 32-bit offsets
+    for walls in (False, True):
+        for nx in (1, 2, 3, 4, 5, 64, 130):
+            for ny in ((5, 6, 9, 64) if walls else (1, 2, 3, 4, 5, 64)):
+                assert audit(L.LBM_D2Q37, "fp32", walls, False, nx, ny, 1, L.LBM_AUDIT_BATCH) == 0, (walls, nx, ny)
+    # the largest instance lbm_batch_create admits (29,020,049 cells per plane) still fits
+    assert audit(L.LBM_D2Q37, "fp32", False, False, 29020049, 1, 1, L.LBM_AUDIT_BATCH) == 0
+    with pytest.raises(L.LbmError):                          # one cell more does not
+        audit(L.LBM_D2Q37, "fp32", False, False, 450, 64489, 1, L.LBM_AUDIT_BATCH)
+
+
 def test_wrong_wrap_threshold_is_caught(audit):
     # one add cannot wrap x - 5 into [0, 4): with threshold 4 (reach-3 lattices' value) an
     # extent-4 D2Q77 row would read the neighbouring row's cells; the launch uses 5
