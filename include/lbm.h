@@ -201,11 +201,12 @@ int lbm_debug_inject_stall(lbm_handle *h, int on);
 
 /* Host-side audit of the stream-collide kernels' addressing (tests only; no device work,
  * no paper counterpart).  For the configuration *p and kernel variant (LBM_KERNEL_DIRECT,
- * LBM_KERNEL_PAIRED, LBM_KERNEL_TWOPASS or LBM_AUDIT_BATCH), forms every element index
- * the variant gathers from and stores to (and, with walls, those of the wall kernel),
- * for every computed cell, with the kernels' own index helpers and
+ * LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED, LBM_KERNEL_TWOPASS or LBM_AUDIT_BATCH), forms
+ * every element index the variant gathers from and stores to (and, with walls, those of
+ * the wall kernel), for every computed cell, with the kernels' own index helpers and
  * the launch's wrap threshold, and counts the accesses outside the 2 Q planes of a
- * population buffer (and the 32-bit accesses of the paired kernel off a 4-byte boundary).
+ * population buffer (and the 32-bit accesses of the paired kernel off a 4-byte boundary,
+ * the staged kernel's bulk copies off a 16-byte boundary).
  * wrap_threshold > 0 replaces the launch's threshold (extents below it take the modulo
  * wrap) so a test can show that a wrong one is caught; 0 keeps the launch's.  Returns the
  * count (0: every access in bounds), or minus an LBM status for invalid parameters or a

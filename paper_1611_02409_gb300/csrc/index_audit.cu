@@ -228,6 +228,64 @@ void audit_batch(const KParams<LAT_D2Q37> &kp, int walls, int x, int y, Tally &t
     }
 }
 
+// k_stream_collide_tma (staged, D2Q37): per tile of TW cells (x0, y, z) and plane p, the
+// bulk copies of the source row segment [x0 - H, x0 + TW + H) (three pieces at a periodic
+// seam) into the stage row; each copy must lie in the buffer, start 16-byte aligned at
+// both ends and move a multiple of 16 bytes; then each cell's read stage[p][H + tx - c_x]
+// must hold the element the definition names.
+template <int ST, bool WALLS> void audit_staged(const KParams<LAT_D2Q37> &kp, int x0, int y, int z, Tally &t)
+{
+    constexpr int LAT = LAT_D2Q37, Q = Lattice<LAT>::Q;
+    using G = TileGeom<ST>;
+    constexpr long long sz = sizeof(typename G::T);
+    const bool small_y = kp.ny < 4;
+    const bool interior = x0 >= G::H && x0 + G::TW + G::H <= kp.nx;
+    for (int p = 0; p < 2 * Q; ++p) {
+        const int i = p < Q ? p : p - Q;
+        const int cx = Lattice<LAT>::T.c[i][0], cy = Lattice<LAT>::T.c[i][1];
+        int ys;
+        if (WALLS) {
+            ys = y - cy + kp.gh;
+        } else {
+            ys = y - cy;
+            if (small_y) ys = ((ys % kp.ny) + kp.ny) % kp.ny;
+            else ys += ys < 0 ? kp.ny : (ys >= kp.ny ? -kp.ny : 0);
+        }
+        const long long row = (long long)p * kp.plane + ((long long)z * kp.nys + ys) * kp.nx;
+        // stage index j -> global element, from the copies issued
+        long long src_of[G::L];
+        auto copy = [&](int j0, long long e0, int n) {
+            t.check(e0);
+            t.check(e0 + n - 1);
+            if ((e0 * sz) % 16 != 0 || ((long long)n * sz) % 16 != 0 ||
+                ((long long)(p * G::L + j0) * sz) % 16 != 0)
+                ++t.bad;
+            for (int j = 0; j < n; ++j) src_of[j0 + j] = e0 + j;
+        };
+        if (interior) {
+            copy(0, row + (x0 - G::H), G::L);
+        } else {
+            const int xl = x0 == 0 ? kp.nx - G::H : x0 - G::H;
+            const int xr = x0 + G::TW == kp.nx ? 0 : x0 + G::TW;
+            copy(0, row + xl, G::H);
+            copy(G::H, row + x0, G::TW);
+            copy(G::H + G::TW, row + xr, G::H);
+        }
+        for (int tx = 0; tx < G::TW; ++tx) {
+            const int j = G::H + tx - cx;
+            if (j < 0 || j >= G::L) {
+                ++t.bad;
+                continue;
+            }
+            t.check(src_of[j], want_src(kp, p / Q, i, x0 + tx, y, z));
+        }
+    }
+    for (int tx = 0; tx < G::TW; ++tx) {
+        const long long o = cell_index<LAT>(kp, x0 + tx, y + kp.gh, z);
+        for (int p = 0; p < 2 * Q; ++p) t.check(o + kp.soff[p] / sz, own_elem(kp, p, x0 + tx, y, z));
+    }
+}
+
 template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wrap)
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
@@ -238,6 +296,21 @@ template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wr
     const int kWrap = wrap > 0 ? wrap : wrap_threshold<LAT>();
     const bool sx = c.nx < kWrap, sy = c.ny < kWrap, sz = c.nz < kWrap;
     const int y0 = c.walls ? 1 : 0, ncomp = c.walls ? c.ny - 2 : c.ny;
+    if constexpr (LAT == LAT_D2Q37) {
+        if (variant == LBM_KERNEL_STAGED) {
+            // the tiles the launch enumerates: (nx / TW) per row, ncomp rows
+            const int TW = c.storage == 0 ? TileGeom<ST_FP32>::TW : TileGeom<ST_FP16>::TW;
+            for (int tile = 0; tile < (c.nx / TW) * ncomp; ++tile) {
+                const int x0 = (tile % (c.nx / TW)) * TW, y = y0 + (tile / (c.nx / TW)) % ncomp;
+                if (c.storage == 0) audit_staged<ST_FP32, WALLS>(kp, x0, y, 0, t);
+                else audit_staged<ST_FP16, WALLS>(kp, x0, y, 0, t);   // FP16 and BF16: 2-byte values
+            }
+            if constexpr (WALLS)
+                for (int b = 0; b < 2; ++b)
+                    for (int x = 0; x < c.nx; ++x) audit_walls<LAT>(kp, x, b, 0, t);
+            return t.bad;
+        }
+    }
     for (int z = 0; z < (D == 3 ? c.nz : 1); ++z)
         for (int yy = 0; yy < ncomp; ++yy)
             for (int x = 0; x < c.nx; ++x) {
@@ -278,11 +351,13 @@ extern "C" long long lbm_debug_index_audit(const lbm_params *p, int variant, int
     if (rc != LBM_OK && rc != LBM_WARN_PR_RANGE) return -rc;
     const bool d2q37_16 = p->lattice == LBM_D2Q37 && p->storage != LBM_FP32;
     if (variant == LBM_KERNEL_PAIRED && !(d2q37_16 && !c.open_x && c.nx % 2 == 0)) return -LBM_ERR_ARG;
+    if (variant == LBM_KERNEL_STAGED && !(p->lattice == LBM_D2Q37 && !c.open_x && c.nx % 128 == 0))
+        return -LBM_ERR_ARG;   // what the staged launch admits
     if (variant == LBM_AUDIT_BATCH &&
         !(p->lattice == LBM_D2Q37 && p->storage == LBM_FP32 && !c.open_x && 2LL * Q * c.plane < (1LL << 31)))
         return -LBM_ERR_ARG;   // what lbm_batch_create admits
     if (variant != LBM_KERNEL_DIRECT && variant != LBM_KERNEL_TWOPASS && variant != LBM_KERNEL_PAIRED &&
-        variant != LBM_AUDIT_BATCH)
+        variant != LBM_KERNEL_STAGED && variant != LBM_AUDIT_BATCH)
         return -LBM_ERR_ARG;
     if (wrap_threshold < 0) return -LBM_ERR_ARG;
     switch (p->lattice) {

@@ -52,6 +52,18 @@ def test_3d(audit, walls):
             assert audit(L.LBM_D3Q103, "fp32", walls, False, nx, ny, nz, v) == 0, (nx, ny, nz, v)
 
 
+def test_staged_kernel_copies(audit):
+    # the staged kernel's bulk copies (in the buffer, 16-byte aligned at both ends, sizes
+    # multiples of 16) and its shared-memory reads against the definition
+    for storage in ("fp32", "fp16", "bf16"):
+        for walls in (False, True):
+            for nx in (128, 256, 384):
+                for ny in ((5, 6, 9) if walls else (1, 2, 3, 4, 9)):
+                    assert audit(L.LBM_D2Q37, storage, walls, False, nx, ny, 1, L.LBM_KERNEL_STAGED) == 0
+    with pytest.raises(L.LbmError):
+        audit(L.LBM_D2Q37, "fp32", nx=130, variant=L.LBM_KERNEL_STAGED)   # nx not a multiple of 128
+
+
 def test_batched_step(audit):
     # one instance of the batched step (D2Q37, FP32): same definition, 32-bit offsets
     for walls in (False, True):
