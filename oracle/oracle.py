@@ -20,6 +20,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(HERE, "liblbm_oracle.so")
+# A prebuilt oracle library to load instead (tests that plant a mistake in a copy of the
+# oracle point this at the mutant's build); the default is built from SRC.
+LIB_OVERRIDE = os.environ.get("LBM_ORACLE_LIB")
 
 D2Q37 = 1
 D3Q103 = 2
@@ -32,13 +35,22 @@ _lock = threading.Lock()
 _lib = None
 
 
+def build_at(src: str, out: str) -> str:
+    """Compile an oracle source file into a shared library (strict IEEE double: no FMA
+    contraction)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-shared", "-fPIC", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (strict IEEE double: no FMA contraction)."""
+    if LIB_OVERRIDE:
+        return LIB_OVERRIDE
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-shared", "-fPIC", "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        build_at(SRC, tmp)
         os.replace(tmp, LIB)
     return LIB
 
@@ -47,8 +59,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(LIB)
+            L = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             ip = C.POINTER(C.c_int)
             L.orc_create.restype = C.c_void_p

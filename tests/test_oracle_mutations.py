@@ -1,0 +1,78 @@
+"""The oracle's pins are not vacuous: a plausible mistake planted in a copy of the oracle
+(a wrong sign, a dropped term, a transposed or reversed index, the wrong temperature in a
+relaxation target) must make the pin that guards that part fail.  Each mutant is built
+from a textual edit of oracle/lbm_oracle.c in a temporary directory and the pin runs
+against it in a child process (LBM_ORACLE_LIB); the unmutated oracle passes the same pins
+in the rest of the suite."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (what the mistake is, source text, replacement, the pin that must catch it)
+MUTANTS = [
+    ("energy populations relax toward T_eq instead of T_rel (reading R1)",
+     "ho[i] = h[i] - om * (h[i] - 0.5 * S->k.Nf * st.Trel * G[i]);",
+     "ho[i] = h[i] - om * (h[i] - 0.5 * S->k.Nf * st.Teq * G[i]);",
+     "tests/test_oracle_equilibrium.py::test_collision_conserves_mass_momentum_energy"),
+    ("Grad's Hermite polynomials without the alternating sign (Sec. IV)",
+     "double term = (P->npairs & 1) ? -1.0 : 1.0;",
+     "double term = 1.0;",
+     "tests/test_oracle_hermite.py::test_hermite_poly_vs_numpy"),
+    ("Eq. fESCoe without its (-1)^(alpha-beta)",
+     "double sign = ((alpha - beta) & 1) ? -1.0 : 1.0;",
+     "double sign = 1.0;",
+     "tests/test_oracle_hermite.py::test_hermite_coeff_vs_quadrature"),
+    ("ES tensor with nu on the isotropic instead of the stress part (Sec. II)",
+     "k->nuG * s->sigma[a * D + b])",
+     "(1.0 - k->nuG) * s->sigma[a * D + b])",
+     "tests/test_oracle_transport.py::test_viscosity_and_conductivity_give_set_Pr"),
+    ("shifted mapping with tau_q = tau/Pr (reading R3)",
+     "k->tau_q = (tau - 0.5) / Pr + 0.5;",
+     "k->tau_q = tau / Pr;",
+     "tests/test_oracle_transport.py::test_viscosity_and_conductivity_give_set_Pr"),
+    ("pull-stream from x + c_i instead of x - c_i (Sec. V)",
+     "int xs = x - S->L.c[i][0];\n                        /* open ends",
+     "int xs = x + S->L.c[i][0];\n                        /* open ends",
+     "tests/test_oracle_shock_tube.py::test_shock_tube_matches_exact_riemann_solution"),
+    ("wall density from the ghost rows instead of the fluid rows (reading R5)",
+     "leaving += g[orc_cell(S, xs, yw + n * s + S->gh, zs) * Q + i];",
+     "leaving += g[orc_cell(S, xs, yw - n * s + S->gh, zs) * Q + i];",
+     "tests/test_oracle_transport.py::test_walls_conserve_fluid_mass"),
+    ("D2Q77 expanded to fifth instead of sixth order (reading R19)",
+     "orc_build_htab(&S->L, lattice == ORC_D2Q77 ? 6 : 4, &S->T);",
+     "orc_build_htab(&S->L, lattice == ORC_D2Q77 ? 5 : 4, &S->T);",
+     "tests/test_oracle_transport.py::test_sixth_order_transport_is_galilean_invariant"),
+    ("a D2Q77 shell mistyped, (5,2) for (5,3) (reading R19)",
+     "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 3, 0}};",
+     "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 2, 0}};",
+     "tests/test_oracle_lattice.py::test_d2q77_moments_degree13"),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_its_pin(tmp_path, what, old, new, pin):
+    src = open(O.SRC).read()
+    assert src.count(old) == 1, "mutation site not unique"
+    mut = tmp_path / "lbm_oracle.c"
+    mut.write_text(src.replace(old, new))
+    so = O.build_at(str(mut), str(tmp_path / "liblbm_oracle.so"))
+    env = dict(os.environ, LBM_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", pin],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 1, (what, r.returncode, r.stdout[-2000:])   # 1: tests ran and failed
+
+
+def test_unmutated_copy_passes_the_same_harness(tmp_path):
+    # the harness itself (copy, build, child run) does not make pins fail
+    so = O.build_at(O.SRC, str(tmp_path / "liblbm_oracle.so"))
+    env = dict(os.environ, LBM_ORACLE_LIB=so)
+    pins = sorted({m[3] for m in MUTANTS})
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider"] + pins,
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:]
