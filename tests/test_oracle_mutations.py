@@ -48,6 +48,14 @@ MUTANTS = [
      "orc_build_htab(&S->L, lattice == ORC_D2Q77 ? 6 : 4, &S->T);",
      "orc_build_htab(&S->L, lattice == ORC_D2Q77 ? 5 : 4, &S->T);",
      "tests/test_oracle_transport.py::test_sixth_order_transport_is_galilean_invariant"),
+    ("open x ends wrapping instead of clamping at the right end (reading R16)",
+     "xs = S->open_x ? (xs < 0 ? 0 : (xs > S->nx - 1 ? S->nx - 1 : xs)) : orc_mod(xs, S->nx);",
+     "xs = S->open_x ? (xs < 0 ? 0 : (xs > S->nx - 1 ? 0 : xs)) : orc_mod(xs, S->nx);",
+     "tests/test_oracle_shock_tube.py::test_open_ends_keep_an_undisturbed_state"),
+    ("a Table D2Q33 shell mistyped, (3,1) for (2,1)",
+     "{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 2, 0}, {3, 0, 0}, {2, 1, 0}, {4, 4, 0}};",
+     "{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 2, 0}, {3, 0, 0}, {3, 1, 0}, {4, 4, 0}};",
+     "tests/test_oracle_lattice.py::test_d2q33_matches_printed_table"),
     ("a D2Q77 shell mistyped, (5,2) for (5,3) (reading R19)",
      "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 3, 0}};",
      "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 2, 0}};",
