@@ -84,3 +84,47 @@ def test_unmutated_copy_passes_the_same_harness(tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider"] + pins,
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+# mistakes planted in the surrogate network's reference (oracle/mlp_oracle.py)
+MLP_MUTANTS = [
+    ("GELU derivative without its z phi(z) term",
+     "return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)",
+     "return 0.5 * (1.0 + erf(z / np.sqrt(2.0)))",
+     "test_gelu_derivative_by_finite_differences"),
+    ("loss gradient normalised by the batch instead of every output",
+     "dz = 2.0 * (y - t) / n",
+     "dz = 2.0 * (y - t) / y.shape[0]",
+     "test_backprop_matches_finite_differences"),
+    ("Adam step divided by v instead of sqrt(v)",
+     "p[j] -= lr * mh / (np.sqrt(vh) + eps)",
+     "p[j] -= lr * mh / (vh + eps)",
+     "test_adam_first_step_closed_form"),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pin", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_planted_mlp_mistake_fails_its_pin(tmp_path, what, old, new, pin):
+    src_dir = os.path.join(ROOT, "oracle")
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    for f in ("__init__.py", "oracle.py", "mlp_oracle.py", "lbm_oracle.c"):
+        text = open(os.path.join(src_dir, f)).read()
+        if f == "mlp_oracle.py":
+            assert text.count(old) == 1, "mutation site not unique"
+            text = text.replace(old, new)
+        (pkg / f).write_text(text)
+    # the child runs from tmp_path, so `import oracle` resolves to the mutated copy
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]),
+               LBM_ORACLE_LIB=O.build())
+    where = subprocess.run([sys.executable, "-c", "import oracle.mlp_oracle as M; print(M.__file__)"],
+                           cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=120)
+    assert where.stdout.strip().startswith(str(pkg)), where.stdout      # the copy is the one loaded
+    test = os.path.join(ROOT, "tests", "test_oracle_mlp.py") + "::" + pin
+    args = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "--rootdir", ROOT, test]
+    r = subprocess.run(args, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, (what, r.returncode, r.stdout[-2000:])
+    # and the same pin passes on an unmutated copy run the same way
+    (pkg / "mlp_oracle.py").write_text(open(os.path.join(src_dir, "mlp_oracle.py")).read())
+    r0 = subprocess.run(args, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r0.returncode == 0, r0.stdout[-2000:]
