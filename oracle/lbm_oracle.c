@@ -40,12 +40,12 @@
  *       first fluid row (populations minus their own Maxwellian).  In 3-D (D3Q103)
  *       the same per wall column (x, z), periodic in x and z.
  *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta.
+ *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
+ *       stream in from outside the x range is the boundary cell's own of that velocity.
  *   R19 D2Q77 (shells 00,10,11,20,21,22,30,31,32,33,40,41,44,50,53; scale r the root of
  *       its augmented degree-13 moment system) stands in for the degree-13 lattice that
  *       the sixth-order expansion needs and the paper does not give; on it the
  *       equilibrium is expanded to order 6.
- *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
- *       stream in from outside the x range is the boundary cell's own of that velocity.
  */
 #include <math.h>
 #include <stdlib.h>
