@@ -60,6 +60,22 @@ MUTANTS = [
      "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 3, 0}};",
      "{3, 2, 0}, {3, 3, 0}, {4, 0, 0}, {4, 1, 0}, {4, 4, 0}, {5, 0, 0}, {5, 2, 0}};",
      "tests/test_oracle_lattice.py::test_d2q77_moments_degree13"),
+    ("heat flux without the internal-energy (h) term (reading C-10)",
+     "qa[d] += 0.5 * v2 * v[d] * g[i] + v[d] * h[i];",
+     "qa[d] += 0.5 * v2 * v[d] * g[i];",
+     "tests/test_oracle_moments.py::test_heat_flux_of_a_third_order_hermite_term"),
+    ("heat flux without the 1/2 of the kinetic part (reading C-10)",
+     "qa[d] += 0.5 * v2 * v[d] * g[i] + v[d] * h[i];",
+     "qa[d] += v2 * v[d] * g[i] + v[d] * h[i];",
+     "tests/test_oracle_moments.py::test_heat_flux_of_a_third_order_hermite_term"),
+    ("heat flux about xi + u instead of the peculiar velocity xi - u",
+     "v[d] = S->L.r * S->L.c[i][d] - st.u[d]; v2 += v[d] * v[d]; }\n                        for (int d = 0; d < D; ++d) qa[d]",
+     "v[d] = S->L.r * S->L.c[i][d] + st.u[d]; v2 += v[d] * v[d]; }\n                        for (int d = 0; d < D; ++d) qa[d]",
+     "tests/test_oracle_moments.py::test_heat_flux_vanishes_for_gaussians_and_pressure_is_rho_lambda"),
+    ("total energy without the 1/2 of the kinetic part (Sec. V, rho E)",
+     "E += 0.5 * x2 * g + S->h[c * Q + i];",
+     "E += x2 * g + S->h[c * Q + i];",
+     "tests/test_oracle_moments.py::test_totals_equal_sums_of_the_moment_fields"),
 ]
 
 
