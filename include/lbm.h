@@ -227,8 +227,9 @@ long long lbm_debug_index_audit(const lbm_params *p, int variant, int wrap_thres
  *   Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream); the call
  *   does not synchronise.  Limit: n <= 33,554,432 cells, else LBM_ERR_ARG.
  * The block partial sums live in one fixed 96 KiB __device__ array inside the library,
- * held on every GPU that loads it until the process exits.  The first call on each
- * device looks that array's address up (cudaGetSymbolAddress) with the device current,
+ * held on every GPU that loads it until the process exits.  Each call made outside a
+ * stream capture looks that array's address up (cudaGetSymbolAddress) with the device
+ * current; a call inside a capture reuses the address of the last call on that device,
  * so make a first call on each device before any stream capture.  Every call shares the
  * array and its last contents; each call overwrites the rows it reads, so nothing needs
  * clearing, but calls that overlap on the GPU (other streams, other threads) race on it.

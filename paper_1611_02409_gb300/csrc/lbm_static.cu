@@ -106,20 +106,28 @@ __global__ void __launch_bounds__(kThreads) k_field_totals_final(const double *_
 }
 
 // Device address of the scratch on the current device (host code must not pass the
-// symbol itself: on the host it names a stand-in, not device memory).
-int scratch_address(double **out)
+// symbol itself: on the host it names a stand-in, not device memory).  The address is
+// looked up again on every call made outside a stream capture, so a context that was
+// torn down and recreated (cudaDeviceReset) gets the array's new address; inside a
+// capture the address of the last call on this device is used.
+int scratch_address(cudaStream_t st, double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return lbm::set_global_error(LBM_ERR_CUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return lbm::set_global_error(LBM_ERR_ARG, "device ordinal out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return lbm::set_global_error(LBM_ERR_CUDA, cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         double *p = nullptr;
         e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_scratch);
         if (e != cudaSuccess || !p)
             return lbm::set_global_error(LBM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return lbm::set_global_error(LBM_ERR_ARG, "first call on this device made during a stream capture");
     }
     *out = g_scratch_ptr[dev];
     return LBM_OK;
@@ -137,11 +145,11 @@ extern "C" int lbm_field_totals_static(int D, double N_f, long long n, const dou
     if (n > kMaxCells)
         return lbm::set_global_error(LBM_ERR_ARG, "n exceeds the static scratch limit of 33554432 cells "
                                                   "(2048 blocks x 16384 cells)");
+    cudaStream_t st = (cudaStream_t)stream;
     double *scratch = nullptr;
-    int rc = scratch_address(&scratch);
+    int rc = scratch_address(st, &scratch);
     if (rc) return rc;
     const int nblk = (int)((n + kChunk - 1) / kChunk);
-    cudaStream_t st = (cudaStream_t)stream;
     k_field_totals<<<nblk, kThreads, 0, st>>>(rho, u, T, n, D, 0.5 * (D + N_f), scratch);
     k_field_totals_final<<<1, kThreads, 0, st>>>(scratch, nblk, out);
     cudaError_t e = cudaGetLastError();

@@ -186,7 +186,7 @@ def _ptr(x):
     if x is None:
         return None, None
     if hasattr(x, "data_ptr"):
-        if x.dtype.itemsize != 8 or not x.is_contiguous():
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous():
             raise ValueError("fields must be contiguous float64")
         return C.c_void_p(x.data_ptr()), (LBM_MEM_DEVICE if x.is_cuda else LBM_MEM_HOST)
     if x.dtype != np.float64 or not x.flags.c_contiguous:
@@ -270,8 +270,23 @@ def lbm_autotune(h, steps=10) -> int:
 
 def lbm_field_totals_static(D, N_f, rho, u, T, out, stream=None):
     """Conservation totals of device fields into the device array `out` (6 doubles),
-    without any allocation; see include/lbm.h."""
+    without any allocation; see include/lbm.h.  The kernel reads rho, u and T and writes
+    out through raw device pointers, so each must be a contiguous float64 CUDA tensor on
+    the current device, u must hold D n values, T n and out at least 6 (ValueError
+    otherwise, before any device work)."""
+    import torch
+    xs = (("rho", rho), ("u", u), ("T", T), ("out", out))
+    for name, x in xs:
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, x in xs:
+        if x.device.index != dev:
+            raise ValueError(f"{name} lives on cuda:{x.device.index}, not on the current device cuda:{dev}")
     n = rho.numel()
+    if u.numel() != int(D) * n or T.numel() != n or out.numel() < 6:
+        raise ValueError(f"sizes: u needs D*n = {int(D) * n} values (has {u.numel()}), T n = {n} "
+                         f"(has {T.numel()}), out at least 6 (has {out.numel()})")
     s = C.c_void_p(stream) if isinstance(stream, int) else C.c_void_p(getattr(stream, "cuda_stream", 0) or 0)
     return _check(lib().lbm_field_totals_static(int(D), float(N_f), n, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0],
                                                 _ptr(out)[0], s))

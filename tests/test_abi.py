@@ -88,3 +88,33 @@ def test_batch_rejects_instances_beyond_32bit_offsets(L, nx, ny, walls):
     h = C.c_void_p()
     assert L.lib().lbm_batch_create(1, C.byref(p), C.byref(h)) == L.LBM_ERR_ARG
     assert b"2^31" in L.lib().lbm_last_error(None)
+
+
+@pytest.mark.parametrize("D,Nf,n,null,what", [
+    (4, 3.0, 1000, False, "D must be 2 or 3"),
+    (1, 3.0, 1000, False, "D must be 2 or 3"),
+    (2, -1.0, 1000, False, "N_f"),
+    (2, float("nan"), 1000, False, "N_f"),
+    (2, 3.0, 1000, True, "null pointer"),
+    (2, 3.0, 0, False, "n must be"),
+    (3, 3.0, 33554433, False, "33554432"),
+])
+def test_field_totals_static_refusals_without_gpu(L, D, Nf, n, null, what):
+    # every refusal of the allocation-free totals is decided from the arguments alone,
+    # before any CUDA call, so it needs no GPU; the pointers are never dereferenced
+    fake = None if null else C.c_void_p(0x1000)
+    rc = L.lib().lbm_field_totals_static(D, Nf, n, fake, C.c_void_p(0x2000), C.c_void_p(0x3000),
+                                         C.c_void_p(0x4000), None)
+    assert rc == L.LBM_ERR_ARG
+    assert what in L.lbm_last_error()
+
+
+def test_field_totals_static_wrapper_checks_arguments(L):
+    # host arrays or wrong dtypes never reach the library (the kernel would be given a host
+    # pointer); on a machine without CUDA the check still refuses before any device call
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        L.lbm_field_totals_static(2, 3.0, x, torch.zeros(16, dtype=torch.float64), x, torch.zeros(6, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        L.lbm_field_totals_static(2, 3.0, np.zeros(8), np.zeros(16), np.zeros(8), np.zeros(6))
