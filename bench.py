@@ -249,6 +249,72 @@ def oracle_mlups(seconds=12.0, n=512):
             "sample": f"{n}x{n} thermal Taylor-Green sample of the workload, {steps} FP64 steps in {dt:.1f} s"}
 
 
+_ORACLE_TIMER = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+from oracle import oracle as O
+from paper_1611_02409_gb300 import inputs
+kind, seconds = sys.argv[2], float(sys.argv[3])
+prm = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
+if kind == "d3q103_32":
+    n = 32
+    o = O.Sim(O.D3Q103, nx=n, ny=n, nz=n, **prm)
+    o.init(*inputs.taylor_green_3d(n, U0=0.02, T_amp=0.01, noise=1e-6))
+    cells = n ** 3
+elif kind == "d2q37_64":
+    o = O.Sim(O.D2Q37, nx=64, ny=64, **prm)
+    o.init(*inputs.shear_thermal_wave(64, 64, noise=1e-6, seed=0))
+    cells = 64 * 64
+else:
+    n = 1024
+    o = O.Sim(O.D2Q37, nx=n, ny=n, **prm)
+    o.init(*inputs.taylor_green_2d(n))
+    cells = n * n
+o.step(1)
+steps, t0 = 0, time.perf_counter()
+while time.perf_counter() - t0 < seconds:
+    o.step(1)
+    steps += 1
+dt = time.perf_counter() - t0
+print(json.dumps({"mlups": cells * steps / dt / 1e6, "steps": steps, "seconds": dt}))
+"""
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), and its logical core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return name, os.cpu_count() or 1
+
+
+def oracle_baselines(seconds=3.0):
+    """The oracle, as it stands, single-threaded and on all host cores, on the three CPU
+    baseline workloads: the 64^2 shear and thermal wave, the 32^3 copy of the 3-D
+    Taylor-Green vortex (D3Q103) and a 1024^2 Taylor-Green sample.  Each timing runs in
+    a fresh process (the OpenMP thread count is fixed at its start) for about `seconds`."""
+    name, ncpu = cpu_model()
+    out = {"cpu_model": name, "nproc": ncpu, "seconds_per_timing": seconds, "unit": "MLUPS"}
+    for kind in ("d2q37_64", "d3q103_32", "d2q37_1024"):
+        row = {}
+        for threads in (1, ncpu):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            try:
+                r = subprocess.run([sys.executable, "-c", _ORACLE_TIMER, ROOT, kind, str(seconds)], env=env,
+                                   capture_output=True, text=True, timeout=600)
+                row[f"threads_{threads}"] = json.loads(r.stdout.strip().splitlines()[-1])
+            except Exception as e:
+                row[f"threads_{threads}"] = {"error": f"{type(e).__name__}: {e}"}
+        out[kind] = row
+    return out
+
+
 def bench_3d(torch, lbm, steps, warmup, peak, n=256):
     """256^3 thermal Taylor-Green vortex on D3Q103 (FP32 and FP16 storage)."""
     from paper_1611_02409_gb300 import inputs
@@ -296,7 +362,7 @@ def accuracy_3d(lbm, n=32, steps=100):
     return out
 
 
-def bench_batch(torch, lbm, steps):
+def bench_batch(torch, lbm, steps, peak):
     """The 512-instance sweep (256 Taylor-Green squares + 256 Couette channels) in one
     batch: tile autotuned, then `steps` graph-replayed steps timed on the device."""
     from paper_1611_02409_gb300 import sweep
@@ -312,26 +378,29 @@ def bench_batch(torch, lbm, steps):
     secs = time.perf_counter() - t0
     ncomp = sum(c["params"]["nx"] * (c["params"]["ny"] - (2 if c["kind"] == "channel" else 0)) for c in cases)
     bt.close()
+    mlups = ncomp * done / secs / 1e6
     return {"workload": "512 instances: 256 periodic thermal Taylor-Green squares (side 64..512) + 256 thermal "
                         "Couette channels 4 x H (H 64..512), seeded Pr, gamma, tau, wall Mach, dT; D2Q37 FP32",
-            "cells": ncomp, "steps": done, "tile": tile, "seconds": secs,
-            "mlups": ncomp * done / secs / 1e6, "timing": "host wall clock around graph replays, synchronised"}
+            "cells": ncomp, "steps": done, "tile": tile, "seconds": secs, "mlups": mlups,
+            "frac": mlups * 1e6 * 2 * Q * 2 * 4 / 1e9 / peak, "timing": "host wall clock around graph replays, "
+                                                                         "synchronised"}
 
 
 def bench_couette(lbm):
-    """The Pr x gamma thermal Couette grid (4 x 256, U = 0.05, T 1.0 / 1.02), one batch:
-    steps to residual 1e-8, then nine decay times of the slowest thermal mode more; u and
-    T profiles against the analytic steady solution (Eq. CouetteDi3, unequal walls).  The
-    same grid at 4 x 64, where FP32 resolves the viscous heating, gives the fitted heating
-    curvature against the analytic one."""
+    """The Pr x gamma thermal Couette grid (4 x 256, U = 0.05, T 1.0 / 1.02, tau = 1), one
+    batch: steps to residual 1e-8, then nine decay times of the slowest thermal mode more;
+    u and T profiles and the fitted viscous-heating curvature against the analytic steady
+    solution (Eq. CouetteDi3, unequal walls).  The same grid at 4 x 64 with tau for
+    nu = 0.02 lattice units as a second case."""
     from paper_1611_02409_gb300 import sweep
-    nu = 0.02
-    res = {"workload": "thermal Couette 4xH, top wall U=0.05 T=1.02, bottom T=1.0, tau=0.528655, "
-                       "Pr x gamma = {0.5,0.71,1,2} x {1.3,1.4,1.67}, FP32, one batch",
+    r2 = lbm.lbm_lattice_table(lbm.LBM_D2Q37)[1] ** 2
+    res = {"workload": "thermal Couette 4xH, top wall U=0.05 T=1.02, bottom T=1.0, Pr x gamma = "
+                       "{0.5,0.71,1,2} x {1.3,1.4,1.67}, FP32, one batch; H=256 at tau=1, H=64 at tau=0.528655",
            "errors": "u: max|u - U eta| / U; T: max|T - T_analytic| / (T_top - T_bottom); "
                      "curvature: fitted viscous-heating coefficient / Pr U^2 / (D+N_f+2)"}
-    for H in (256, 64):
-        cases = sweep.couette_grid(H=H)
+    for H, tau in ((256, 1.0), (64, 0.528655)):
+        nu = (tau - 0.5) / r2
+        cases = sweep.couette_grid(H=H, tau=tau)
         settle = int(9 * (H - 1) ** 2 / (np.pi ** 2 * nu / max(sweep.COUETTE_PR)))
         out = sweep.run_couette(lbm, cases, tol=1e-8, settle_steps=settle, check_every=1000)
         eta = np.arange(H) / (H - 1)
@@ -347,7 +416,7 @@ def bench_couette(lbm):
             curv = float(np.linalg.lstsq(A, out["profiles_settled"][i][1] - (1.0 + dT * eta), rcond=None)[0][0] / heat)
             rows.append(dict(Pr=float(Pr), gamma=float(gamma), steps_to_1e8=int(out["steps_to_tol"][i]),
                              u_err_at_1e8=eu8, T_err_at_1e8=eT8, u_err=eu, T_err=eT, curvature_ratio=curv))
-        res[f"H{H}"] = {"settle_steps": settle, "seconds_to_1e8": out["seconds_to_tol"],
+        res[f"H{H}"] = {"tau": tau, "settle_steps": settle, "seconds_to_1e8": out["seconds_to_tol"],
                         "seconds_settle": out["seconds_settle"], "all_converged": bool(out["converged"].all()),
                         "max_u_err": max(r["u_err"] for r in rows), "max_T_err": max(r["T_err"] for r in rows),
                         "curvature_ratio_range": [min(r["curvature_ratio"] for r in rows),
@@ -356,19 +425,54 @@ def bench_couette(lbm):
     return res
 
 
+def gate_errors(f, prof):
+    """Relative L2 errors of GPU channel fields [ny, nx] against the oracle's steady
+    profiles [ny] (rho, u as a vector field, T)."""
+    col = lambda v: np.repeat(v[:, None], f["rho"].shape[1], axis=1)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    uo = np.stack([col(prof[:, 1]), col(prof[:, 2])])
+    return dict(rho=rel(f["rho"], col(prof[:, 0])), u=rel(f["u"], uo), T=rel(f["T"], col(prof[:, 3])))
+
+
 def bench_warm_start(lbm):
     """The learned warm start: surrogate trained on 256 steady channels (H 64..128), then
-    256 held-out 4 x 256 channels from rest and from its prediction, to residual 1e-8."""
-    from paper_1611_02409_gb300 import surrogate
-    res, _ = surrogate.study(lbm, refine=False)
+    256 held-out 4 x 256 channels from rest and from its prediction, to residual 1e-8.
+    Gate against the FP64 oracle: six held-out channels (H 33..65) that the oracle settled
+    to within 1e-11 of their steady state (tests/golden/couette_steady_oracle.txt), run
+    from rest and from the prediction until the distance to the steady state is bounded
+    by 1e-8 (FP64 storage) or 1e-6 (FP32 storage, capped at 60 decay times); final field
+    error of each against the oracle."""
+    from paper_1611_02409_gb300 import surrogate, sweep
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    from make_couette_steady import load
+    res, _ = surrogate.study(lbm, refine=False, keep_model=True)
+    sur = res.pop("model")
     t = res["test"]
-    return {"workload": "256 held-out thermal Couette channels 4x256, seeded Pr, gamma, Ma, tau, dT; surrogate "
-                        "5-512-512-512-512-1024 trained on 256 channels of height 64..128 by the lbm_mlp kernels",
-            "steps_rest_median": t["steps_rest_median"], "steps_warm_median": t["steps_warm_median"],
-            "step_ratio_median": t["step_ratio_median"], "batch_seconds_rest": t["batch_seconds_rest"],
-            "batch_seconds_warm": t["batch_seconds_warm"], "converged": [t["rest_converged"], t["warm_converged"]],
-            "state_diff_at_1e8": t["state_diff_at_tol"],
-            "train_seconds": res["train"]["seconds_total"], "final_loss": res["train"]["losses"][-1][1]}
+    out = {"workload": "256 held-out thermal Couette channels 4x256, seeded Pr, gamma, Ma, tau, dT; surrogate "
+                       "5-512-512-512-512-1024 trained on 256 channels of height 64..128 by the lbm_mlp kernels",
+           "steps_rest_median": t["steps_rest_median"], "steps_warm_median": t["steps_warm_median"],
+           "step_ratio_median": t["step_ratio_median"], "batch_seconds_rest": t["batch_seconds_rest"],
+           "batch_seconds_warm": t["batch_seconds_warm"], "converged": [t["rest_converged"], t["warm_converged"]],
+           "state_diff_at_1e8": t["state_diff_at_tol"],
+           "train_seconds": res["train"]["seconds_total"], "final_loss": res["train"]["losses"][-1][1]}
+    gold = load()
+    cases = [sweep.channel_case(c["Pr"], c["gamma"], c["Ma"], c["tau"], c["dT"], c["H"]) for c, _ in gold]
+    pred = sur.predict(np.array([c["inputs"] for c in cases]))
+    gate = {"channels": [c["H"] for c, _ in gold]}
+    for storage, bound in (("fp64", 1e-8), ("fp32", 1e-6)):
+        rows = surrogate.gate_study(lbm, cases, pred, bound=bound, storage=storage)
+        g = {"distance_bound": bound}
+        for start in ("rest", "warm"):
+            errs = [gate_errors(r[start]["fields"], prof) for r, (_, prof) in zip(rows, gold)]
+            g[start] = {"err_vs_oracle_max": max(max(e.values()) for e in errs),
+                        "err_u_max": max(e["u"] for e in errs), "err_T_max": max(e["T"] for e in errs),
+                        "steps_median": float(np.median([r[start]["steps"] for r in rows])),
+                        "seconds_total": float(sum(r[start]["seconds"] for r in rows)),
+                        "reached_bound": int(sum(r[start]["distance_bound"] <= bound for r in rows))}
+        g["step_ratio_median"] = float(np.median([r["warm"]["steps"] / r["rest"]["steps"] for r in rows]))
+        gate[storage] = g
+    out["gate_vs_oracle"] = gate
+    return out
 
 
 def bench_shock_tube(torch, lbm, peak, steps_tp=100):
@@ -454,6 +558,54 @@ def bench_mode_study(lbm):
                                "T_err": st["T_err"], "u_err": st["u_err"]}
     out["couette_steady_seconds"] = pc["steady_seconds"]
     return out
+
+
+def sig(x, n=4):
+    """Floats rounded to n significant digits, recursively (keeps the JSON line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{n}g}") if np.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: sig(v, n) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, n) for v in x]
+    return x
+
+
+def summarize(name, d):
+    """The short form of one extra measurement for the JSON line (the full form goes to
+    the --details file): per-case arrays are reduced to their extremes."""
+    if not isinstance(d, dict) or "error" in d:
+        return d
+    if name == "couette_grid":
+        return {"workload": d["workload"],
+                **{h: {k: d[h][k] for k in ("tau", "all_converged", "max_u_err", "max_T_err",
+                                             "curvature_ratio_range", "settle_steps")}
+                   for h in ("H256", "H64") if h in d}}
+    if name == "mode_study":
+        out = {}
+        for m in ("shifted", "literal"):
+            rows = d["transport"][m]
+            out[f"{m}_Pr_meas_over_pred"] = [min(r["Pr_meas"] / r["Pr_pred"] for r in rows.values()),
+                                             max(r["Pr_meas"] / r["Pr_pred"] for r in rows.values())]
+            c = d[f"couette_{m}"]
+            out[f"couette_{m}"] = {"heating_ratio": c["heating_ratio"], "heating_ratio_set_Pr": c["heating_ratio_set_Pr"],
+                                   "startup_max_err": max(c["startup_max_err"].values()), "u_err": c["u_err"]}
+        return out
+    if name == "accuracy":
+        return {k: ({f: v[f] for f in ("rho", "u", "T")} if isinstance(v, dict) else v) for k, v in d.items()}
+    if name == "d3q103_256":
+        out = {st: {k: d[st][k] for k in ("mlups", "frac", "launch_ms")} for st in ("fp32", "fp16") if st in d}
+        acc = d.get("accuracy", {})
+        out["err_vs_oracle_32cube"] = {st: acc[st]["max_rel"] for st in ("fp32", "fp16") if st in acc}
+        return out
+    if name == "burnett_d2q77":
+        return {st: {k: d[st][k] for k in ("mlups", "frac")} for st in ("fp32", "fp16") if st in d}
+    if name == "batched_sweep":
+        return {k: d[k] for k in ("cells", "steps", "tile", "mlups", "frac") if k in d}
+    if name == "warm_start":
+        return {k: d[k] for k in ("steps_rest_median", "steps_warm_median", "step_ratio_median",
+                                  "batch_seconds_rest", "batch_seconds_warm", "gate_vs_oracle") if k in d}
+    return d
 
 
 def _extra(out, name, fn):
@@ -557,13 +709,15 @@ def run_ours(args):
         # the other configurations, measured at one GPU only (they hold no other rank)
         _extra(extra, "accuracy", lambda: accuracy_vs_oracle(lbm))
         _extra(extra, "d3q103_256", lambda: bench_3d(torch, lbm, max(args.steps // 8, 20), args.warmup, peak))
-        _extra(extra, "batched_sweep", lambda: bench_batch(torch, lbm, max(args.steps // 2, 100)))
+        _extra(extra, "batched_sweep", lambda: bench_batch(torch, lbm, max(args.steps // 2, 100), peak))
         _extra(extra, "couette_grid", lambda: bench_couette(lbm))
         _extra(extra, "warm_start", lambda: bench_warm_start(lbm))
         _extra(extra, "shock_tube_d2q33", lambda: bench_shock_tube(torch, lbm, peak))
         _extra(extra, "mode_study", lambda: bench_mode_study(lbm))
         _extra(extra, "burnett_d2q77", lambda: bench_burnett(torch, lbm, peak))
-        extra["cpu_baseline"] = oracle_mlups()
+        cpu = oracle_mlups()
+        _extra(cpu, "workloads", oracle_baselines)
+        extra["cpu_baseline"] = cpu
     if rank != 0:
         return
     r32 = results["fp32"]
@@ -586,13 +740,25 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "lbm_init_fields from pinned host rho,u,T + K steps + lbm_moments of rho,u,T to pinned "
                         "host; bytes per step are the field copies divided by K"},
-        "storage_variants": {
-            s: {"mlups": results[s]["mlups"], "ms_per_step": results[s]["total_ms"] / results[s]["steps"],
-                "launch_ms": results[s]["launch_ms"], "achieved_gbs": results[s]["achieved"],
-                "frac": results[s]["achieved"] / peak, "algorithmic_bytes_per_cell": results[s]["b_cell"],
-                "steps": results[s]["steps"]} for s in ("fp16", "bf16")},
     }
-    line.update(extra)
+    variants = {s: {"mlups": results[s]["mlups"], "ms_per_step": results[s]["total_ms"] / results[s]["steps"],
+                    "launch_ms": results[s]["launch_ms"], "achieved_gbs": results[s]["achieved"],
+                    "frac": results[s]["achieved"] / peak, "algorithmic_bytes_per_cell": results[s]["b_cell"],
+                    "steps": results[s]["steps"]} for s in ("fp16", "bf16")}
+    if args.details:
+        full = dict(line, storage_variants=variants, **extra)
+        with open(args.details, "w") as f:
+            json.dump(full, f, indent=1, default=float)
+    # the line: headline keys first, then each extra's short form, the storage forms last
+    # (the headline keys unrounded; the extras to four significant digits)
+    if "cpu_baseline" in extra:
+        line["cpu_baseline"] = sig(extra.pop("cpu_baseline"))
+    for name in ("mode_study", "shock_tube_d2q33", "batched_sweep", "couette_grid", "burnett_d2q77", "warm_start",
+                 "d3q103_256", "accuracy"):
+        if name in extra:
+            line[name] = sig(summarize(name, extra.pop(name)))
+    line.update(sig(extra))
+    line["storage_variants"] = sig({s: {k: v[k] for k in ("mlups", "frac", "launch_ms")} for s, v in variants.items()})
     print(json.dumps(line), flush=True)
 
 
@@ -604,6 +770,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--extras", default="all", choices=["all", "none"],
                     help="none: only the timed 4096^2 runs (for profiler launch lists)")
+    ap.add_argument("--details", default=None,
+                    help="write every measurement in full (per-case arrays included) to this JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -66,12 +66,17 @@ extern "C" {
 #define LBM_PR_SHIFTED 0
 #define LBM_PR_LITERAL 1
 
-/* population storage (arithmetic is FP32 in every case): every precision holds
- * (g_i - w_i)/w_i and (h_i - w_i N_f/2)/w_i, the deviations from the rest state
- * rho = T = 1, u = 0 scaled by the weight; FP16 / BF16 round to nearest even. */
+/* population storage: every precision holds (g_i - w_i)/w_i and (h_i - w_i N_f/2)/w_i,
+ * the deviations from the rest state rho = T = 1, u = 0 scaled by the weight.  FP32, FP16
+ * and BF16 storage compute in FP32 (FP16 / BF16 round to nearest even when stored).
+ * LBM_FP64 stores and computes in FP64 (D2Q37 and D3Q103, two-pass kernel only, twice the
+ * bytes of FP32): for steady states that must match an FP64 reference more closely than
+ * the FP32 iteration allows, whose fixed points wander by a few 1e-6 of u with the path
+ * taken to them.  No paper counterpart: the paper states no precision. */
 #define LBM_FP32 0
 #define LBM_FP16 1
 #define LBM_BF16 2
+#define LBM_FP64 3
 
 /* y boundaries */
 #define LBM_PERIODIC 0
@@ -107,7 +112,7 @@ typedef struct lbm_params {
     double kappa;         /* ES-BGK kappa in (0, 1]; kappa = 1 forces Pr = 1               */
     double tau;           /* tau_f = tau / dt in lattice steps, > 1/2                      */
     int pr_mode;          /* LBM_PR_SHIFTED or LBM_PR_LITERAL                              */
-    int storage;          /* LBM_FP32, LBM_FP16 or LBM_BF16                                */
+    int storage;          /* LBM_FP32, LBM_FP16, LBM_BF16 or LBM_FP64                      */
     int nx, ny, nz;       /* grid; nz = 1 for D = 2; nx, ny >= 1 (walls: ny >= 5);
                              ny (+ 4 with walls) and nz at most 65535                        */
     int bc_y;             /* LBM_PERIODIC or LBM_WALLS (D2Q37, D3Q103; walls are the planes
@@ -147,11 +152,13 @@ int lbm_coefficients(const lbm_handle *h, double *out);
 int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w);
 int lbm_map_params(const lbm_params *p, double *out);
 
-/* Sets every population (domain and wall ghost rows) to the discrete equilibrium of the
- * fields with Lambda = T delta: g_i = G_i(rho, u, T delta), h_i = (N_f/2) T G_i.  rho[n],
- * u[D][n], T[n] with n = Nx Ny Nz; ghost rows take the nearest domain row's field.
- * `mem` = LBM_MEM_DEVICE or LBM_MEM_HOST (host arrays are staged through a device copy
- * on the handle's stream).  Resets the step counter. */
+/* Sets every domain population to the discrete equilibrium of the fields with
+ * Lambda = T delta: g_i = G_i(rho, u, T delta), h_i = (N_f/2) T G_i.  rho[n], u[D][n],
+ * T[n] with n = Nx Ny Nz.  With walls, the wall procedure then rebuilds the wall and ghost
+ * rows from the first fluid rows, as after every step, so the fluid rows keep exactly
+ * their initial mass from the first step on (the wall rows' reported fields are then the
+ * wall procedure's, not the input's).  `mem` = LBM_MEM_DEVICE or LBM_MEM_HOST (host arrays
+ * are staged through a device copy on the handle's stream).  Resets the step counter. */
 int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const double *T, int mem);
 
 /* lbm_init_fields plus a non-equilibrium part (warm start from predicted profiles;

@@ -39,7 +39,9 @@
  *       wall values through the first fluid row, non-equilibrium part copied from the
  *       first fluid row (populations minus their own Maxwellian).  In 3-D (D3Q103)
  *       the same per wall column (x, z), periodic in x and z.
- *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta.
+ *   R6  initial populations are the equilibrium of the given fields with Lambda = T delta;
+ *       with walls, the wall procedure (R5) then rebuilds the wall and ghost rows from the
+ *       first fluid rows, as after every step.
  *   R16 the shock tube's open ends (Sec. VI B) are zero-gradient: a population that would
  *       stream in from outside the x range is the boundary cell's own of that velocity.
  *   R19 D2Q77 (shells 00,10,11,20,21,22,30,31,32,33,40,41,44,50,53; scale r the root of
@@ -619,6 +621,8 @@ void orc_destroy(void *p)
     free(S);
 }
 
+static void orc_walls(orc_sim *S, double *g, double *h);
+
 /* Fields are SoA [component][z][y][x] over the Nx x Ny (x Nz) domain. */
 int orc_init(void *p, const double *rho, const double *u, const double *T)
 {
@@ -639,6 +643,10 @@ int orc_init(void *p, const double *rho, const double *u, const double *T)
                 orc_maxwell_pops(S, rho[f], uu, T[f], S->g + c * Q, S->h + c * Q);
             }
         }
+    /* reading R6: the wall procedure fills the wall and ghost rows from the initial fluid
+     * rows, as after every step, so the first streaming exchanges mass with the walls in
+     * balance too: the fluid rows keep exactly their initial mass from the start */
+    if (S->walls) orc_walls(S, S->g, S->h);
     S->steps = 0;
     return 0;
 }

@@ -290,7 +290,7 @@ template <int LAT, bool WALLS> long long audit(const Ctx &c, int variant, int wr
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
     const KParams<LAT> kp = make_kparams<LAT>(c);
-    const long long elem = c.storage == 0 ? 4 : 2;
+    const long long elem = storage_bytes(c.storage);
     Tally t;
     t.total = 2LL * Q * c.plane;
     const int kWrap = wrap > 0 ? wrap : wrap_threshold<LAT>();
@@ -349,7 +349,8 @@ extern "C" long long lbm_debug_index_audit(const lbm_params *p, int variant, int
     double r = 0.0;
     const int rc = make_ctx(*p, c, &D, &Q, &r);
     if (rc != LBM_OK && rc != LBM_WARN_PR_RANGE) return -rc;
-    const bool d2q37_16 = p->lattice == LBM_D2Q37 && p->storage != LBM_FP32;
+    const bool d2q37_16 = p->lattice == LBM_D2Q37 && (p->storage == LBM_FP16 || p->storage == LBM_BF16);
+    if (p->storage == LBM_FP64 && variant != LBM_KERNEL_TWOPASS) return -LBM_ERR_ARG;   // two-pass only
     if (variant == LBM_KERNEL_PAIRED && !(d2q37_16 && !c.open_x && c.nx % 2 == 0)) return -LBM_ERR_ARG;
     if (variant == LBM_KERNEL_STAGED && !(p->lattice == LBM_D2Q37 && !c.open_x && c.nx % 128 == 0))
         return -LBM_ERR_ARG;   // what the staged launch admits

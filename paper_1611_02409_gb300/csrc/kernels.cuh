@@ -40,8 +40,11 @@ template <int C> LBM_HD __forceinline__ int src_x(int x, int n, bool small, bool
     return wrap_sub<C>(x, n, small);
 }
 
-template <int LAT>
-LBM_HD __forceinline__ long long cell_index(const KParams<LAT> &kp, int x, int ys, int z)
+// Launch parameters of the kernels of storage form ST (FP64 constants for FP64 storage).
+template <int LAT, int ST> using KParamsOf = KParams<LAT, typename Storage<ST>::R>;
+
+template <int LAT, class S>
+LBM_HD __forceinline__ long long cell_index(const KParams<LAT, S> &kp, int x, int ys, int z)
 {
     return ((long long)z * kp.nys + ys) * kp.nx + x;
 }
@@ -62,9 +65,9 @@ template <int ELEM> struct StrideOff {
 // `cell` is the destination cell's address in set 0 plane 0; off(I) the planes' byte offsets.
 // With V = f2 (two neighbouring cells, 16-bit storage) both lanes are relaxed by packed
 // FMAs and stored as one 32-bit word at the first cell's address.
-template <int LAT, int ST, class Off, class V>
+template <int LAT, int ST, class Off, class V, class S>
 __device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ cell, const Off &off, int I,
-                                            float om, const EqScalT<V> &z, V q, V s, V t)
+                                            S om, const EqScalT<V> &z, V q, V s, V t)
 {
     using T = typename Storage<ST>::T;
     constexpr int Q = Lattice<LAT>::Q;
@@ -73,12 +76,12 @@ __device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict_
         static_assert(ST != ST_FP32, "paired cells use 16-bit storage");
         Storage<ST>::st2(reinterpret_cast<T *>(b + off(I)), vfma(f2(z.om1), s, vfma(f2(om), q, z.wdrho)));
         Storage<ST>::st2(reinterpret_cast<T *>(b + off(Q + I)), vfma(f2(z.om1), t, vfma(z.whr, q, z.whb)));
-    } else if constexpr (ST == ST_FP32) {
+    } else if constexpr (ST == ST_FP32 || ST == ST_FP64) {
         // difference form: the non-equilibrium part G~/w - s is formed exactly
-        const float Gs = z.drho + q;
-        const float Ht = fmaf(z.hr, q, z.hb);
-        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), fmaf(om, Gs - s, s));
-        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), fmaf(om, Ht - t, t));
+        const V Gs = z.drho + q;
+        const V Ht = vfma(z.hr, q, z.hb);
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), vfma(om, Gs - s, s));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), vfma(om, Ht - t, t));
     } else {
         // (1 - omega) s + omega G~/w in two FMAs (z carries omega-scaled terms); its extra
         // FP32 rounding is far below the 16-bit storage rounding
@@ -88,8 +91,8 @@ __device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict_
 }
 
 // Collide one cell's streamed populations (accessor `pop`) and store them at offset o.
-template <int LAT, int ST, class Pop, class Off = TableOff>
-__device__ __forceinline__ void collide_store(const KParams<LAT> &kp, const Pop &pop,
+template <int LAT, int ST, class Pop, class Off = TableOff, class S = float>
+__device__ __forceinline__ void collide_store(const KParams<LAT, S> &kp, const Pop &pop,
                                               typename Storage<ST>::T *__restrict__ dst, long long o,
                                               const Off &off = Off{nullptr})
 {
@@ -140,7 +143,7 @@ template <int LAT, int ST> constexpr int direct_min_blocks() { return Lattice<LA
 template <int LAT, int ST, bool WALLS>
 __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_collide(const typename Storage<ST>::T *__restrict__ src,
                                                         typename Storage<ST>::T *__restrict__ dst,
-                                                        const KParams<LAT> kp, int small_x, int small_y,
+                                                        const KParamsOf<LAT, ST> kp, int small_x, int small_y,
                                                         int small_z)
 {
     constexpr int D = Lattice<LAT>::D;
@@ -185,13 +188,13 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
     (void)small_z;
     // keep the conversions (and everything after) below the whole gather
     asm volatile("" ::: "memory");
-    float s[Q], t[Q];
+    typename S::R s[Q], t[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         s[i] = S::cvt(rs[i]);
         t[i] = S::cvt(rt[i]);
     }
-    collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o);
+    collide_store<LAT, ST>(kp, ArrayPopT<typename S::R>{s, t}, dst, o);
 }
 
 // Populations read from the source buffer where they are used (two-pass kernel): a cell's
@@ -204,8 +207,8 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
 // the buffer address opaque, so the relaxation reads the values again (from L1 / L2)
 // instead of keeping the moment pass's values live across the cell.
 template <int LAT, int ST, int CH> struct GatherPop {
-    using V = float;
     using S = Storage<ST>;
+    using V = typename S::R;
     using T = typename S::T;
     static constexpr int Q = Lattice<LAT>::Q;
     static constexpr int NP = (Q - 1) / 2;
@@ -234,12 +237,12 @@ template <int LAT, int ST, int CH> struct GatherPop {
             asm volatile("" ::: "memory");
         }
     }
-    template <int I> __device__ __forceinline__ float sv() const
+    template <int I> __device__ __forceinline__ V sv() const
     {
         if constexpr (I == 0) return S::ld(src + at<0>());
         else return S::cvt(bs[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
-    template <int I> __device__ __forceinline__ float tv() const
+    template <int I> __device__ __forceinline__ V tv() const
     {
         if constexpr (I == 0) return S::ld(src + Q * plane + at<0>());
         else return S::cvt(bt[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
@@ -256,12 +259,16 @@ template <int LAT> constexpr int twopass_chunk() { return Lattice<LAT>::D == 2 ?
 // passes, so the kernel fits a lattice whose 2Q values would not (D3Q103, 206 values):
 // more resident warps in exchange for a second, cache-served read.  Every cell takes the
 // same tabulated-offset gather (no seam divergence).
-template <int LAT> constexpr int twopass_min_blocks() { return Lattice<LAT>::D == 2 ? 4 : 2; }
+// FP64 storage (double arithmetic, twice the registers per value): two blocks per SM.
+template <int LAT, int ST> constexpr int twopass_min_blocks()
+{
+    return ST == ST_FP64 ? 2 : (Lattice<LAT>::D == 2 ? 4 : 2);
+}
 
 template <int LAT, int ST, bool WALLS>
-__global__ void __launch_bounds__(128, twopass_min_blocks<LAT>()) k_stream_collide_2p(
+__global__ void __launch_bounds__(128, twopass_min_blocks<LAT, ST>()) k_stream_collide_2p(
     const typename Storage<ST>::T *__restrict__ src, typename Storage<ST>::T *__restrict__ dst,
-    const KParams<LAT> kp, int small_x, int small_y, int small_z)
+    const KParamsOf<LAT, ST> kp, int small_x, int small_y, int small_z)
 {
     constexpr int D = Lattice<LAT>::D;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,27 +478,27 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
 }
 
 // Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].
-template <int LAT>
-__device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho, const float (&v)[Lattice<LAT>::D],
-                                             float th, float *s, float *t)
+template <int LAT, class S>
+__device__ __forceinline__ void maxwell_pops(const KParams<LAT, S> &kp, S drho, const S (&v)[Lattice<LAT>::D], S th,
+                                             S *s, S *t)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
-    EqState<D> e;
+    EqState<D, S> e;
     maxwell_state<D>(drho, v, kp.r, kp.R2_hi, th, e);
-    PolyCoef<D, float, Lattice<LAT>::ORDER> pc;
+    PolyCoef<D, S, Lattice<LAT>::ORDER> pc;
     poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
-    const EqScal z = eq_scalars<D>(e, kp.halfNf);
+    const EqScalT<S> z = eq_scalars<D>(e, kp.halfNf);
     s[0] = z.drho + pc.k[0];
-    t[0] = fmaf(z.hr, pc.k[0], z.hb);
+    t[0] = vfma(z.hr, pc.k[0], z.hb);
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
-        float E, O;
+        S E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
         s[I] = z.drho + (E + O);
-        t[I] = fmaf(z.hr, E + O, z.hb);
+        t[I] = vfma(z.hr, E + O, z.hb);
         s[I + 1] = z.drho + (E - O);
-        t[I + 1] = fmaf(z.hr, E - O, z.hb);
+        t[I + 1] = vfma(z.hr, E - O, z.hb);
     });
 }
 
@@ -504,7 +511,7 @@ __device__ __forceinline__ void maxwell_pops(const KParams<LAT> &kp, float drho,
 // the translational share (D+2)/(D+2+N_f) to g through the third Hermite term
 // s_i += (xi^2 - D - 2)(q_g . xi)/(D + 2), the internal share to h, t_i += q_h . xi.
 template <int LAT, int ST>
-__global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<LAT> kp,
+__global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParamsOf<LAT, ST> kp,
                        const double *__restrict__ rho, const double *__restrict__ u,
                        const double *__restrict__ T, const double *__restrict__ Pi, const double *__restrict__ q)
 {
@@ -517,35 +524,36 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<
     y = y < 0 ? 0 : (y > kp.ny - 1 ? kp.ny - 1 : y);
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
-    float vv[D];
+    using R = typename Storage<ST>::R;
+    R vv[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) vv[a] = (float)(u[a * n + f] / (double)kp.r_d);
-    float s[Q], t[Q];
-    maxwell_pops<LAT>(kp, (float)(rho[f] - 1.0), vv, (float)(T[f] - 1.0), s, t);
+    for (int a = 0; a < D; ++a) vv[a] = (R)(u[a * n + f] / (double)kp.r_d);
+    R s[Q], t[Q];
+    maxwell_pops<LAT>(kp, (R)(rho[f] - 1.0), vv, (R)(T[f] - 1.0), s, t);
     if (Pi || q) {
-        float P[D][D], qg[D], qh[D];
+        R P[D][D], qg[D], qh[D];
         const double rT = rho[f] * T[f];
         int k = 0;
         for (int a = 0; a < D; ++a)
             for (int b = a; b < D; ++b) {
                 const double v = Pi ? Pi[(k++) * n + f] - (a == b ? rT : 0.0) : 0.0;
-                P[a][b] = P[b][a] = (float)v;
+                P[a][b] = P[b][a] = (R)v;
             }
-        float tr = 0.f;
+        R tr = 0.f;
         for (int a = 0; a < D; ++a) tr += P[a][a];
         for (int a = 0; a < D; ++a) P[a][a] -= tr / D;
         const double share = (D + 2.0) / (D + 2.0 + kp.Nf);
         for (int a = 0; a < D; ++a) {
             const double qa = q ? q[a * n + f] : 0.0;
-            qg[a] = (float)(qa * share);
-            qh[a] = (float)(qa * (1.0 - share));
+            qg[a] = (R)(qa * share);
+            qh[a] = (R)(qa * (1.0 - share));
         }
         static_for<0, Q>([&](auto II) {
             constexpr int I = decltype(II)::value;
-            float xi[D], x2 = 0.f, qgx = 0.f, qhx = 0.f, pxx = 0.f;
+            R xi[D], x2 = 0.f, qgx = 0.f, qhx = 0.f, pxx = 0.f;
             static_for<0, D>([&](auto AA) {
                 constexpr int a = decltype(AA)::value;
-                xi[a] = kp.r * (float)cv<LAT, I, a>();
+                xi[a] = kp.r * (R)cv<LAT, I, a>();
             });
             for (int a = 0; a < D; ++a) {
                 x2 += xi[a] * xi[a];
@@ -553,7 +561,7 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<
                 qhx += qh[a] * xi[a];
                 for (int b = 0; b < D; ++b) pxx += P[a][b] * xi[a] * xi[b];
             }
-            s[I] += 0.5f * pxx + (x2 - (float)(D + 2)) * qgx / (float)(D + 2);
+            s[I] += R(0.5) * pxx + (x2 - (R)(D + 2)) * qgx / (R)(D + 2);
             t[I] += qhx;
         });
     }
@@ -566,8 +574,8 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParams<
 }
 
 template <int LAT, int ST>
-__device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> &kp,
-                                          long long o, float *s, float *t)
+__device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> &kp,
+                                          long long o, typename Storage<ST>::R *s, typename Storage<ST>::R *t)
 {
     constexpr int Q = Lattice<LAT>::Q;
 #pragma unroll
@@ -584,82 +592,89 @@ __device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restr
 // rho_w G(1, u_k, T_k delta) + the first fluid row's non-equilibrium (populations minus
 // their Maxwellian).  rho_w balances exactly the mass the fluid sends into these rows
 // in the next streaming against the mass the rows send back.
-struct WallParams {
-    float vw[2][3];  // wall velocity in lattice units, u_w / r
-    float thw[2];    // T_w - 1
+template <class R = float> struct WallParamsT {
+    R vw[2][3];  // wall velocity in lattice units, u_w / r
+    R thw[2];    // T_w - 1
 };
+using WallParams = WallParamsT<float>;
+
+// Moment sums of the auxiliary kernels (walls, moments, diagnostics): compensated in FP32,
+// plain in FP64.
+template <class R> constexpr bool aux_precise() { return std::is_same<R, float>::value; }
 
 // The wall procedure for one column (x, z) of wall b (0 bottom, 1 top) of buffer `buf`
 // (z = 0 in 2-D; in 3-D the walls are the planes y = 0 and y = ny - 1, periodic in x, z).
 template <int LAT, int ST>
-__device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> &kp,
-                                            const WallParams &wp, int x, int b, int z = 0)
+__device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> &kp,
+                                            const WallParamsT<typename Storage<ST>::R> &wp, int x, int b, int z = 0)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
+    using R = typename Storage<ST>::R;
     static_assert(Lattice<LAT>::R <= 3, "two ghost rows beyond each wall row cover a reach of 3");
     const int n = b == 0 ? 1 : -1;
     const int yw = b == 0 ? 0 : kp.ny - 1;
     const int small_x = kp.nx < 4, small_z = kp.nz < 4;
-    float s1[Q], t1[Q];
+    R s1[Q], t1[Q];
     load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, yw + n + kp.gh, z), s1, t1);
-    RawMoments<D> m;
-    raw_moments<LAT>(kp, ArrayPop{s1, t1}, m);
-    CellState<D> c;
+    RawMoments<D, R> m;
+    raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s1, t1}, m);
+    CellState<D, R> c;
     cell_state<LAT>(kp, m, c);
-    float ms[Q], mt[Q];
+    R ms[Q], mt[Q];
     maxwell_pops<LAT>(kp, c.drho, c.v, c.th_eq, ms, mt);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {  // non-equilibrium of the first fluid row
         s1[i] -= ms[i];
         t1[i] -= mt[i];
     }
-    float uk[3][D], thk[3];   // lattice-unit velocities of the boundary rows
+    R uk[3][D], thk[3];   // lattice-unit velocities of the boundary rows
     for (int k = 0; k <= 2; ++k) {
 #pragma unroll
         for (int a = 0; a < D; ++a) uk[k][a] = wp.vw[b][a] - k * (c.v[a] - wp.vw[b][a]);
         thk[k] = wp.thw[b] - k * (c.th_eq - wp.thw[b]);
     }
     // unit-density equilibria of the boundary rows (deviation / w): drho = 0
-    float gk[3][Q], hk[3][Q];
-    for (int k = 0; k <= 2; ++k) maxwell_pops<LAT>(kp, 0.f, uk[k], thk[k], gk[k], hk[k]);
+    R gk[3][Q], hk[3][Q];
+    for (int k = 0; k <= 2; ++k) maxwell_pops<LAT>(kp, R(0), uk[k], thk[k], gk[k], hk[k]);
     // leaving - B - A, all in deviation form: the w parts of "leaving" and "A" cancel.
-    float Ld = 0.f, Bd = 0.f, Ad = 0.f, W = 0.f;
+    R Ld = 0.f, Bd = 0.f, Ad = 0.f, W = 0.f;
     static_for<0, Q>([&](auto II) {
         constexpr int I = decltype(II)::value;
         constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
         if constexpr (cy != 0) {
             const int cn = cy * n;
-            const float w = kp.w[I];
+            const R w = kp.w[I];
             if (cn < 0) {
                 const int xs = wrap_sub<cx>(x, kp.nx, small_x);
                 const int zs = D == 3 ? wrap_sub<cz>(z, kp.nz, small_z) : 0;
                 for (int sdist = 1; sdist <= -cn; ++sdist)
-                    Ld = fmaf(w, Storage<ST>::ld(buf + (long long)I * kp.plane
+                    Ld = vfma(w, Storage<ST>::ld(buf + (long long)I * kp.plane
                                                  + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, zs)), Ld);
             } else {
-                W = fmaf((float)cn, w, W);
-                Bd = fmaf((float)cn * w, s1[I], Bd);
-                for (int k = 0; k < cn; ++k) Ad = fmaf(w, gk[k][I], Ad);
+                W = vfma((R)cn, w, W);
+                Bd = vfma((R)cn * w, s1[I], Bd);
+                for (int k = 0; k < cn; ++k) Ad = vfma(w, gk[k][I], Ad);
             }
         }
     });
-    const float drw = (Ld - Bd - Ad) / (W + Ad);   // rho_w - 1
-    const float rw = 1.f + drw;
+    const R drw = (Ld - Bd - Ad) / (W + Ad);   // rho_w - 1
+    const R rw = 1.f + drw;
     for (int k = 0; k <= 2; ++k) {
         const long long o = cell_index<LAT>(kp, x, yw - n * k + kp.gh, z);
         // G(rho_w, u_k, T_k)/w - 1 = drw + rw * gk;   (N_f/2)(rho_w T_k G/w - 1) = drw' + rw * hk
-        const float hb = kp.halfNf * drw;
+        const R hb = kp.halfNf * drw;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            Storage<ST>::st(buf + (long long)i * kp.plane + o, fmaf(rw, gk[k][i], drw) + s1[i]);
-            Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, fmaf(rw, hk[k][i], hb) + t1[i]);
+            Storage<ST>::st(buf + (long long)i * kp.plane + o, vfma(rw, gk[k][i], drw) + s1[i]);
+            Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, vfma(rw, hk[k][i], hb) + t1[i]);
         }
     }
 }
 
 template <int LAT, int ST>
-__global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const WallParams wp)
+__global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> kp,
+                        const WallParamsT<typename Storage<ST>::R> wp)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
@@ -668,19 +683,20 @@ __global__ void k_walls(typename Storage<ST>::T *__restrict__ buf, const KParams
 
 // Macroscopic fields of the stored populations (FP64 out, any pointer may be null).
 template <int LAT, int ST>
-__global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp,
+__global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> kp,
                           double *rho, double *u, double *T, double *Pi, double *q)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
+    using R = typename Storage<ST>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= kp.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
-    float s[Q], t[Q];
+    R s[Q], t[Q];
     load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
-    RawMoments<D> m;
-    raw_moments<LAT>(kp, ArrayPop{s, t}, m);
-    CellState<D> c;
+    RawMoments<D, R> m;
+    raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s, t}, m);
+    CellState<D, R> c;
     cell_state<LAT>(kp, m, c);
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
@@ -697,21 +713,21 @@ __global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const
     if (q) {
         // q_a = sum g |v|^2 v_a / 2 + sum h v_a, v = xi - u; the rest-state (w) part is
         // -u_a (D + 2 + u^2 + N_f)/2 in closed form (degree-3 moments of the lattice).
-        float u2 = 0.f;
+        R u2 = 0.f;
         for (int a = 0; a < D; ++a) u2 += c.u[a] * c.u[a];
-        float qa[D];
-        for (int a = 0; a < D; ++a) qa[a] = -0.5f * c.u[a] * (D + 2 + u2 + kp.Nf);
+        R qa[D];
+        for (int a = 0; a < D; ++a) qa[a] = R(-0.5) * c.u[a] * (D + 2 + u2 + kp.Nf);
         static_for<0, Q>([&](auto II) {
             constexpr int I = decltype(II)::value;
-            const float w = kp.w[I];
-            float v[D], v2 = 0.f;
+            const R w = kp.w[I];
+            R v[D], v2 = 0.f;
             static_for<0, D>([&](auto AA) {
                 constexpr int a = decltype(AA)::value;
-                v[a] = kp.r * (float)cv<LAT, I, a>() - c.u[a];
+                v[a] = kp.r * (R)cv<LAT, I, a>() - c.u[a];
                 v2 += v[a] * v[a];
             });
-            const float gd = w * s[I], hd = w * t[I];
-            for (int a = 0; a < D; ++a) qa[a] += (0.5f * v2 * gd + hd) * v[a];
+            const R gd = w * s[I], hd = w * t[I];
+            for (int a = 0; a < D; ++a) qa[a] += (R(0.5) * v2 * gd + hd) * v[a];
         });
         for (int a = 0; a < D; ++a) q[a * n + f] = qa[a];
     }
@@ -751,11 +767,12 @@ __device__ __forceinline__ void block_sums(double (&acc)[kDiagNV], double *out)
 // next call's residual.
 template <int LAT, int ST>
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const typename Storage<ST>::T *__restrict__ buf,
-                                                        const KParams<LAT> kp, float *snap, int have_snap,
-                                                        double *partials)
+                                                        const KParamsOf<LAT, ST> kp, typename Storage<ST>::R *snap,
+                                                        int have_snap, double *partials)
 {
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
+    using R = typename Storage<ST>::R;
     double acc[kDiagNV];
 #pragma unroll
     for (int v = 0; v < kDiagNV; ++v) acc[v] = 0.0;
@@ -765,18 +782,18 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const typename Storage<ST
         const int x = (int)(f % kp.nx);
         const long long yz = f / kp.nx;
         const int y = (int)(yz % kp.ny), z = (int)(yz / kp.ny);
-        float s[Q], t[Q];
+        R s[Q], t[Q];
         load_cell<LAT, ST>(buf, kp, cell_index<LAT>(kp, x, y + kp.gh, z), s, t);
-        RawMoments<D> m;
-        raw_moments<LAT>(kp, ArrayPop{s, t}, m);
-        CellState<D> c;
+        RawMoments<D, R> m;
+        raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s, t}, m);
+        CellState<D, R> c;
         cell_state<LAT>(kp, m, c);
         acc[0] += (double)m.drho;
         for (int a = 0; a < D; ++a) acc[1 + a] += (double)kp.r * (double)m.J[a];
-        float trM = 0.f;
+        R trM = 0.f;
         for (int a = 0; a < D; ++a) trM += m.M[a][a];
         acc[4] += 0.5 * (double)kp.r * (double)kp.r * (double)trM + (double)m.H;
-        const float ux = c.u[0], th = c.th_eq;
+        const R ux = c.u[0], th = c.th_eq;
         bool ok = isfinite(c.rho) && isfinite(th) && c.rho > 0.f && 1.f + th > 0.f;
         for (int a = 0; a < D; ++a) ok = ok && isfinite(c.u[a]);
         acc[9] += ok ? 0.0 : 1.0;
@@ -799,7 +816,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double *__res
 
 // Domain populations to / from absolute FP64 [i][z][y][x].
 template <int LAT, int ST>
-__global__ void k_get_pops(const typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, double *g,
+__global__ void k_get_pops(const typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> kp, double *g,
                            double *h)
 {
     constexpr int Q = Lattice<LAT>::Q;
@@ -817,7 +834,7 @@ __global__ void k_get_pops(const typename Storage<ST>::T *__restrict__ buf, cons
 }
 
 template <int LAT, int ST>
-__global__ void k_set_pops(typename Storage<ST>::T *__restrict__ buf, const KParams<LAT> kp, const double *g,
+__global__ void k_set_pops(typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> kp, const double *g,
                            const double *h)
 {
     constexpr int Q = Lattice<LAT>::Q;
@@ -829,8 +846,9 @@ __global__ void k_set_pops(typename Storage<ST>::T *__restrict__ buf, const KPar
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
     for (int i = 0; i < Q; ++i) {
         const double w = kp.w[i];
-        Storage<ST>::st(buf + (long long)i * kp.plane + o, (float)(g[i * n + f] / w - 1.0));
-        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, (float)(h[i * n + f] / w - (double)kp.halfNf));
+        using R = typename Storage<ST>::R;
+        Storage<ST>::st(buf + (long long)i * kp.plane + o, (R)(g[i * n + f] / w - 1.0));
+        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, (R)(h[i * n + f] / w - (double)kp.halfNf));
     }
 }
 

@@ -41,7 +41,7 @@ struct lbm_handle {
     int diag_blocks;
     double *d_out;
     double *h_out;         // pinned
-    float *d_snap;         // u_x and T - 1 of the previous diagnostics call
+    void *d_snap;          // u_x and T - 1 of the previous diagnostics call (storage's arithmetic type)
     int have_snap;
     long long snap_step;
     int *d_err;            // [0] error word of the kernels' bounded waits, [1] fault injection
@@ -57,7 +57,7 @@ struct lbm_handle {
 static int default_kernel(const lbm_handle *h)
 {
     if (h->ops.paired_ok(h->ctx)) return LBM_KERNEL_PAIRED;
-    if (h->D == 3 || h->p.lattice == LBM_D2Q77) return LBM_KERNEL_TWOPASS;
+    if (h->D == 3 || h->p.lattice == LBM_D2Q77 || h->p.storage == LBM_FP64) return LBM_KERNEL_TWOPASS;
     return LBM_KERNEL_DIRECT;
 }
 
@@ -150,7 +150,9 @@ static int map_params(const lbm_params &p, Mapped &m)
         return set_err(nullptr, LBM_ERR_ARG, "walls need D2Q37 or D3Q103 and ny >= 5");
     if (p.bc_x != LBM_PERIODIC && p.bc_x != LBM_OPEN) return set_err(nullptr, LBM_ERR_ARG, "bad bc_x");
     if (p.bc_x == LBM_OPEN && D != 2) return set_err(nullptr, LBM_ERR_ARG, "open x ends need D = 2");
-    if (p.storage < LBM_FP32 || p.storage > LBM_BF16) return set_err(nullptr, LBM_ERR_ARG, "bad storage");
+    if (p.storage < LBM_FP32 || p.storage > LBM_FP64) return set_err(nullptr, LBM_ERR_ARG, "bad storage");
+    if (p.storage == LBM_FP64 && p.lattice != LBM_D2Q37 && p.lattice != LBM_D3Q103)
+        return set_err(nullptr, LBM_ERR_ARG, "FP64 storage is built for D2Q37 and D3Q103");
     if (p.pr_mode != LBM_PR_SHIFTED && p.pr_mode != LBM_PR_LITERAL) return set_err(nullptr, LBM_ERR_ARG, "bad pr_mode");
     if (!(p.Pr > 0) || !(p.tau > 0.5) || !(p.kappa > 0) || !(p.kappa <= 1))
         return set_err(nullptr, LBM_ERR_ARG, "need Pr > 0, tau > 1/2, 0 < kappa <= 1");
@@ -309,7 +311,7 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
         c.wall_T[b] = p.wall_T[b];
     }
     h->ops = lbm::ops_for(p.lattice, p.storage);
-    h->elem = p.storage == LBM_FP32 ? 4 : 2;
+    h->elem = (size_t)lbm::storage_bytes(p.storage);
     h->buf_elems = (size_t)2 * h->Q * (size_t)c.plane;
     for (int k = 0; k < 2; ++k) {
         cudaError_t e = cudaMalloc(&h->buf[k], h->buf_elems * h->elem);
@@ -408,6 +410,9 @@ int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const dou
         return set_err(h, LBM_ERR_ARG, "bad mem");
     }
     h->ops.init(h->ctx, h->buf[h->cur], dr, du, dT, h->stream);
+    // the wall and ghost rows from the initial fluid rows, as after every step: the first
+    // streaming then exchanges mass with the walls in balance (reading R6)
+    if (h->ctx.walls) h->ops.walls(h->ctx, h->buf[h->cur], h->stream);
     LBM_CK(h, cudaGetLastError());
     h->steps = 0;
     h->have_snap = 0;
@@ -446,6 +451,7 @@ int lbm_init_fields_neq(lbm_handle *h, const double *rho, const double *u, const
         return set_err(h, LBM_ERR_ARG, "bad mem");
     }
     h->ops.init_neq(h->ctx, h->buf[h->cur], dr, du, dT, dP, dq, h->stream);
+    if (h->ctx.walls) h->ops.walls(h->ctx, h->buf[h->cur], h->stream);
     LBM_CK(h, cudaGetLastError());
     h->steps = 0;
     h->have_snap = 0;
@@ -513,7 +519,8 @@ int lbm_diagnostics(lbm_handle *h, double *out)
     NvtxRange nvtx_("lbm_diagnostics");
     if (!h || !out) return set_err(h, LBM_ERR_ARG, "null argument");
     const long long n = ncell(h);
-    if (!h->d_snap) LBM_CK(h, cudaMalloc(&h->d_snap, sizeof(float) * 2 * n));
+    const size_t snap_elem = h->p.storage == LBM_FP64 ? sizeof(double) : sizeof(float);
+    if (!h->d_snap) LBM_CK(h, cudaMalloc(&h->d_snap, snap_elem * 2 * n));
     h->ops.diag(h->ctx, h->buf[h->cur], h->d_snap, h->have_snap, h->d_partials, h->diag_blocks, h->stream);
     lbm::launch_diag_final(h->d_partials, h->diag_blocks, h->d_out, h->stream);
     LBM_CK(h, cudaGetLastError());
@@ -562,6 +569,8 @@ int lbm_set_kernel(lbm_handle *h, int variant)
     if (variant == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx))
         return set_err(h, LBM_ERR_ARG, "paired kernel needs D = 2, 16-bit storage and nx even");
     if (variant < LBM_KERNEL_DIRECT || variant > LBM_KERNEL_TWOPASS) return set_err(h, LBM_ERR_ARG, "bad variant");
+    if (h->p.storage == LBM_FP64 && variant != LBM_KERNEL_TWOPASS)
+        return set_err(h, LBM_ERR_ARG, "FP64 storage runs on the two-pass kernel only");
     h->ctx.kernel = variant;
     return LBM_OK;
 }
@@ -577,6 +586,7 @@ int lbm_autotune(lbm_handle *h, int steps, int *chosen)
     for (int v = LBM_KERNEL_DIRECT; v <= LBM_KERNEL_TWOPASS; ++v) {
         if (v == LBM_KERNEL_STAGED && !h->ops.staged_ok(h->ctx)) continue;
         if (v == LBM_KERNEL_PAIRED && !h->ops.paired_ok(h->ctx)) continue;
+        if (h->p.storage == LBM_FP64 && v != LBM_KERNEL_TWOPASS) continue;
         h->ctx.kernel = v;
         int rc = lbm_step(h, 2);
         if (rc) return rc;

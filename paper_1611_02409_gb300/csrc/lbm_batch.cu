@@ -446,6 +446,8 @@ int lbm_batch_init_fields_neq(lbm_batch *b, int i, const double *rho, const doub
         }
     }
     Launch<LAT, ST>::init_neq(c, b->d_arena + in.buf[in.cur], dr, du, dT, dP, dq, b->stream);
+    // wall and ghost rows from the initial fluid rows, as lbm_init_fields does
+    if (c.walls) Launch<LAT, ST>::walls(c, b->d_arena + in.buf[in.cur], b->stream);
     in.active = 1;
     in.steps = 0;
     in.have_snap = 0;

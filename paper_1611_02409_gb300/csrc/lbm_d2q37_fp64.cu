@@ -1,0 +1,7 @@
+// Kernel instantiations for one lattice and storage form (one unit each, so the build
+// compiles them in parallel).
+#include "dispatch.cuh"
+
+namespace lbm {
+Ops ops_d2q37_fp64() { return make_ops_st<LAT_D2Q37, ST_FP64>(); }
+} // namespace lbm

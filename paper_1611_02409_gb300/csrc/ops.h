@@ -14,8 +14,12 @@ struct Ctx {
     int *d_err;            // device error word (bounded waits that gave up set it)
     int open_x;            // open (zero-gradient) x ends
     int num_sms;
-    int kernel;            // 1 direct, 2 shared-memory staged
+    int kernel;            // LBM_KERNEL_*: 1 direct, 2 staged, 3 paired, 4 two-pass
 };
+
+// Bytes of one stored population in storage form LBM_FP32 (0), LBM_FP16 (1), LBM_BF16 (2)
+// or LBM_FP64 (3).
+inline int storage_bytes(int storage) { return storage == 0 ? 4 : storage == 3 ? 8 : 2; }
 
 struct Ops {
     void (*init)(const Ctx &, void *dst, const double *rho, const double *u, const double *T, cudaStream_t);
@@ -25,8 +29,8 @@ struct Ops {
     void (*walls)(const Ctx &, void *buf, cudaStream_t);
     void (*moments)(const Ctx &, const void *buf, double *rho, double *u, double *T, double *Pi, double *q,
                     cudaStream_t);
-    void (*diag)(const Ctx &, const void *buf, float *snap, int have_snap, double *partials, int nblk,
-                 cudaStream_t);
+    void (*diag)(const Ctx &, const void *buf, void *snap, int have_snap, double *partials, int nblk,
+                 cudaStream_t);   // snap: 2 n values of the storage's arithmetic type
     void (*get_pops)(const Ctx &, const void *buf, double *g, double *h, cudaStream_t);
     void (*set_pops)(const Ctx &, void *buf, const double *g, const double *h, cudaStream_t);
     bool (*staged_ok)(const Ctx &);
@@ -45,11 +49,14 @@ Ops ops_d2q33_bf16();
 Ops ops_d2q77_fp32();
 Ops ops_d2q77_fp16();
 Ops ops_d2q77_bf16();
+Ops ops_d2q37_fp64();
+Ops ops_d3q103_fp64();
 
 // The launch table of a lattice (LBM_D2Q37 = 1, LBM_D3Q103 = 2, LBM_D2Q33 = 3, LBM_D2Q77 = 4)
-// and storage form.
+// and storage form (FP64 storage: D2Q37 and D3Q103 only, checked by the caller).
 inline Ops ops_for(int lattice, int storage)
 {
+    if (storage == 3) return lattice == 2 ? ops_d3q103_fp64() : ops_d2q37_fp64();
     if (lattice == 1) return storage == 1 ? ops_d2q37_fp16() : storage == 2 ? ops_d2q37_bf16() : ops_d2q37_fp32();
     if (lattice == 3) return storage == 1 ? ops_d2q33_fp16() : storage == 2 ? ops_d2q33_bf16() : ops_d2q33_fp32();
     if (lattice == 4) return storage == 1 ? ops_d2q77_fp16() : storage == 2 ? ops_d2q77_bf16() : ops_d2q77_fp32();

@@ -28,14 +28,16 @@
 
 namespace lbm {
 
-enum : int { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+enum : int { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_FP64 = 3 };
 
-// raw(): the stored bits, cvt(): to FP32.  The gather loads all raw values first and
-// converts them afterwards, so every load of a cell is in flight at once.
+// raw(): the stored bits, cvt(): to the arithmetic type R (FP32, or FP64 for FP64
+// storage).  The gather loads all raw values first and converts them afterwards, so every
+// load of a cell is in flight at once.
 template <int ST> struct Storage;
 template <> struct Storage<ST_FP32> {
     using T = float;
     using Raw = float;
+    using R = float;
     static __device__ __forceinline__ Raw raw(const T *p) { return __ldg(p); }
     static __device__ __forceinline__ float cvt(Raw r) { return r; }
     static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
@@ -44,6 +46,7 @@ template <> struct Storage<ST_FP32> {
 template <> struct Storage<ST_FP16> {
     using T = __half;
     using Raw = unsigned short;
+    using R = float;
     static __device__ __forceinline__ Raw raw(const T *p)
     {
         return __ldg(reinterpret_cast<const unsigned short *>(p));
@@ -69,6 +72,7 @@ template <> struct Storage<ST_FP16> {
 template <> struct Storage<ST_BF16> {
     using T = __nv_bfloat16;
     using Raw = unsigned short;
+    using R = float;
     static __device__ __forceinline__ Raw raw(const T *p)
     {
         return __ldg(reinterpret_cast<const unsigned short *>(p));
@@ -91,8 +95,21 @@ template <> struct Storage<ST_BF16> {
     }
 };
 
-// Per-launch parameters (passed by value; read from the constant bank).
-template <int LAT> struct KParams {
+// FP64 storage with FP64 arithmetic: for steady states that must agree with an FP64
+// reference beyond the fixed-point wander of the FP32 iteration.
+template <> struct Storage<ST_FP64> {
+    using T = double;
+    using Raw = double;
+    using R = double;
+    static __device__ __forceinline__ Raw raw(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ double cvt(Raw r) { return r; }
+    static __device__ __forceinline__ double ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(T *p, double v) { __stcs(p, v); }
+};
+
+// Per-launch parameters (passed by value; read from the constant bank).  S is the
+// arithmetic type of the kernels they serve (float, or double for FP64 storage).
+template <int LAT, class S = float> struct KParams {
     static constexpr int Q = Lattice<LAT>::Q;
     int nx, ny, nz;       // domain
     int nys;              // stored rows (ny + 2 gh)
@@ -100,18 +117,18 @@ template <int LAT> struct KParams {
     int y0, ny_comp;      // first computed domain row and number of computed rows
     int open_x;           // open (zero-gradient) ends in x instead of periodic
     long long plane;      // stored cells per population plane
-    float omega;          // relaxation rate
-    float kappa, a_tr, a_sig; // Lambda = (1-k)[(1-nu) T_tr d + nu sigma] + k T_eq d
-    float Nf, halfNf, r;
+    S omega;              // relaxation rate
+    S kappa, a_tr, a_sig; // Lambda = (1-k)[(1-nu) T_tr d + nu sigma] + k T_eq d
+    S Nf, halfNf, r;
     double r_d;           // r in FP64 (field input conversion)
-    float R2_hi, R2_lo;   // r^2 as an unevaluated float sum (hi + lo)
-    float w[Q];           // lattice weights (FP32), for the wall and flux sums
+    S R2_hi, R2_lo;       // r^2 as an unevaluated sum (hi + lo; lo = 0 in FP64)
+    S w[Q];               // lattice weights, for the wall and flux sums
     // Shell weights as hi + lo float pairs.  Conservation of momentum rests on the
     // identity r^2 sum_i w_i c_i c_i = delta holding for the constants actually used:
     // FP32-rounded r^2 and w_i miss it by ~1e-8, which the over-relaxed collision turns
     // into a systematic drift j -> j (1 + omega eps) per step.  The moment sums therefore
     // use w_hi + w_lo and the linear equilibrium term uses R2_hi + R2_lo.
-    float wsh_hi[Lattice<LAT>::NSHELL], wsh_lo[Lattice<LAT>::NSHELL];
+    S wsh_hi[Lattice<LAT>::NSHELL], wsh_lo[Lattice<LAT>::NSHELL];
     signed char cvel[Q][3]; // integer velocities, for runtime-indexed loops
     // Byte offsets, relative to a cell's own address in set 0 plane 0, of the source of
     // population p (p < Q: g_p, else h_{p-Q}) for a cell away from the periodic seams,
@@ -243,9 +260,8 @@ __device__ __forceinline__ void burnett_terms(const EqState<2, V> &s, float r, P
 // Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!
 // for the fourth-order expansion (Eq. GExpansion); with N = 6 (2-D) the fifth- and
 // sixth-order terms are added.
-template <int D, class V, int N>
-__device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, float R2_hi, float R2_lo,
-                                            PolyCoef<D, V, N> &pc)
+template <int D, class V, int N, class S>
+__device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, S r, S R2_hi, S R2_lo, PolyCoef<D, V, N> &pc)
 {
     const auto &A = s.A;
     const auto &u = s.u;
@@ -296,11 +312,11 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, float r, flo
             c2[a][b] = s.X[a][b]
                      - 0.5f * rho * (trA * A[a][b] + 2.f * A2[a][b] + trA * u[a] * u[b] + 2.f * Au[a] * u[b]
                                      + 2.f * Au[b] * u[a] + u2 * A[a][b] + u2 * u[a] * u[b]);
-    const float r3 = R2_hi * r, r4 = R2_hi * R2_hi;
+    const S r3 = R2_hi * r, r4 = R2_hi * R2_hi;
     static_for<0, Monos<D>::K>([&](auto KK) {
         constexpr int K = decltype(KK)::value;
         constexpr int m = Monos<D>::M.deg[K];
-        constexpr float inv = (float)inv_alpha_factorial<D, K>();
+        constexpr S inv = (S)inv_alpha_factorial<D, K>();
         constexpr int i0 = mono_index<D, K>(0), i1 = mono_index<D, K>(1);
         constexpr int i2 = mono_index<D, K>(2), i3 = mono_index<D, K>(3);
         V v;
@@ -362,20 +378,22 @@ template <int D, class V = float> struct RawMoments {
 // re-converts or re-reads stored values there instead of keeping them live), and
 // prefetch<P>() before the opposite pair P is used (a no-op unless the accessor reads
 // memory in chunks of pairs).
-struct ArrayPop {
-    using V = float;
-    const float *s, *t;
+template <class R = float> struct ArrayPopT {
+    using V = R;
+    const R *s, *t;
     __device__ __forceinline__ void refresh() {}
     template <int P> __device__ __forceinline__ void prefetch() const {}
-    template <int I> __device__ __forceinline__ float sv() const { return s[I]; }
-    template <int I> __device__ __forceinline__ float tv() const { return t[I]; }
+    template <int I> __device__ __forceinline__ R sv() const { return s[I]; }
+    template <int I> __device__ __forceinline__ R tv() const { return t[I]; }
 };
+using ArrayPop = ArrayPopT<float>;
 
 // PRECISE (FP32 storage): hi + lo shell weights and an error-free momentum fold.  The
 // 16-bit storage forms round every population to 2^-11 (FP16) or 2^-8 (BF16) each step,
-// far above these 1e-8 effects, and fold with the FP32 weights alone.
-template <int LAT, bool PRECISE = true, class Pop>
-__device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &pop,
+// far above these 1e-8 effects, and fold with the FP32 weights alone; FP64 storage folds
+// with the FP64 weights (plain double sums).
+template <int LAT, bool PRECISE = true, class Pop, class S>
+__device__ __forceinline__ void raw_moments(const KParams<LAT, S> &kp, const Pop &pop,
                                             RawMoments<Lattice<LAT>::D, typename Pop::V> &m)
 {
     constexpr int D = Lattice<LAT>::D;
@@ -398,7 +416,7 @@ __device__ __forceinline__ void raw_moments(const KParams<LAT> &kp, const Pop &p
     // from cell to cell and from step to step, and the collision would inject it into the
     // conserved momentum as a slow systematic drift.
     auto fold = [&](int sh) {
-        const float wh = kp.wsh_hi[sh], wl = kp.wsh_lo[sh];
+        const S wh = kp.wsh_hi[sh], wl = kp.wsh_lo[sh];
         if constexpr (!PRECISE) {
 #pragma unroll
             for (int k = 0; k < NM; ++k) {
@@ -498,8 +516,8 @@ template <class V> __device__ __forceinline__ V fast_inv(V x);
 template <> __device__ __forceinline__ float fast_inv<float>(float x) { return __fdividef(1.f, x); }
 template <> __device__ __forceinline__ f2 fast_inv<f2>(f2 x) { return f2(__fdividef(1.f, x.x), __fdividef(1.f, x.y)); }
 
-template <int LAT, bool FASTDIV = false, class V>
-__device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMoments<Lattice<LAT>::D, V> &m,
+template <int LAT, bool FASTDIV = false, class V, class S>
+__device__ __forceinline__ void cell_state(const KParams<LAT, S> &kp, const RawMoments<Lattice<LAT>::D, V> &m,
                                            CellState<Lattice<LAT>::D, V> &c)
 {
     constexpr int D = Lattice<LAT>::D;
@@ -526,7 +544,7 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
             c.rsdev[a][b] = c.rsdev[b][a] = v;
             if (a == b) tr += v;
         }
-    c.rth_tr = tr * (1.f / D);
+    c.rth_tr = tr * (S(1) / S(D));
     if (kp.Nf > 0.f) {
         if constexpr (FASTDIV) {
             c.rth_int = __fdividef(2.f, kp.Nf) * m.H - m.drho;
@@ -550,8 +568,8 @@ __device__ __forceinline__ void cell_state(const KParams<LAT> &kp, const RawMome
 // the same tensor as (1-kappa)[(1-nu) T_tr delta + nu sigma] + kappa T_eq delta - delta written so
 // that its trace, D theta_tr + kappa D (theta_eq - theta_tr), does not depend on rounded
 // complements of kappa (energy closes exactly in the collision).
-template <int LAT, class V>
-__device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState<Lattice<LAT>::D, V> &c,
+template <int LAT, class V, class S>
+__device__ __forceinline__ void es_state(const KParams<LAT, S> &kp, const CellState<Lattice<LAT>::D, V> &c,
                                          EqState<Lattice<LAT>::D, V> &e)
 {
     constexpr int D = Lattice<LAT>::D;
@@ -575,9 +593,8 @@ __device__ __forceinline__ void es_state(const KParams<LAT> &kp, const CellState
 }
 
 // Maxwellian state (Lambda = T delta) of (rho, u = r v, T) given the lattice velocity v.
-template <int D>
-__device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], float r, float R2_hi, float th,
-                                              EqState<D> &e)
+template <int D, class R>
+__device__ __forceinline__ void maxwell_state(R drho, const R (&v)[D], R r, R R2_hi, R th, EqState<D, R> &e)
 {
     e.drho = drho;
     e.rho = 1.f + drho;
@@ -602,12 +619,13 @@ __device__ __forceinline__ void maxwell_state(float drho, const float (&v)[D], f
 //   G~_I / w_I = drho + Pq,   H~_I / w_I = (N_f/2)(drho + rho th_rel) + (N_f/2)(1 + th_rel) Pq
 template <class V = float> struct EqScalT {
     V drho, hb, hr;
-    float om1;            // 1 - omega
+    typename ScalarOf<V>::type om1; // 1 - omega
     V wdrho, whb, whr;    // omega-scaled terms (16-bit storage relaxation)
 };
 using EqScal = EqScalT<float>;
 
-template <int D, class V> __device__ __forceinline__ EqScalT<V> eq_scalars(const EqState<D, V> &e, float halfNf)
+template <int D, class V, class S>
+__device__ __forceinline__ EqScalT<V> eq_scalars(const EqState<D, V> &e, S halfNf)
 {
     EqScalT<V> z;
     z.drho = e.drho;

@@ -35,6 +35,7 @@ LBM_PR_LITERAL = 1
 LBM_FP32 = 0
 LBM_FP16 = 1
 LBM_BF16 = 2
+LBM_FP64 = 3
 LBM_PERIODIC = 0
 LBM_WALLS = 1
 LBM_OPEN = 2
@@ -48,7 +49,7 @@ LBM_MLP_GEMM_MMA_SYNC = 1
 LBM_MEM_DEVICE = 0
 LBM_MEM_HOST = 1
 
-STORAGE = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
+STORAGE = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16, "fp64": LBM_FP64}
 
 
 class LbmError(RuntimeError):

@@ -17,7 +17,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="d2q37", choices=["d2q37", "d3q103", "d2q33", "d2q77"])
     ap.add_argument("--grid", type=int, default=2048)
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "staged", "paired", "twopass"])

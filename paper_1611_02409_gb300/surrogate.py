@@ -153,18 +153,77 @@ def state_diff(fa, fb, idx):
     return du, dT
 
 
+def channel_tau_slow(case, r):
+    """Slowest decay time, in steps, of a thermal Couette channel 4 x H near its steady
+    state: the lowest shear mode decays in (H-1)^2 / (pi^2 nu) steps, the lowest thermal
+    mode in Pr times that (chi = nu / Pr under the shifted mapping), with the lattice
+    viscosity nu = (tau - 1/2) / r^2 at T = 1."""
+    p = case["params"]
+    nu = (p["tau"] - 0.5) / r ** 2
+    return (p["ny"] - 1) ** 2 * max(1.0, p["Pr"]) / (np.pi ** 2 * nu)
+
+
+def run_to_steady(sim, tau_slow, bound=1e-8, chunk=200, max_steps=5_000_000):
+    """Steps one handle until its distance to the steady state is bounded by `bound`
+    (relative, u_x and T).  Near a steady state the fields approach it as exp(-n / tau)
+    with tau the slowest decay time, so the per-step change r (lbm_diagnostics' residual,
+    taken over `chunk` steps) and the distance d satisfy d <= r tau; tau is the larger of
+    tau_slow and the decay time measured from successive residuals.  Returns (steps,
+    residual, distance bound)."""
+    sim.diagnostics()
+    steps, prev, res = 0, None, float("inf")
+    while steps < max_steps:
+        sim.step(chunk)
+        steps += chunk
+        res = sim.diagnostics()["residual"]
+        tau_est = chunk / np.log(prev / res) if prev and 0.0 < res < prev else 0.0
+        dist = res * max(tau_slow, tau_est)
+        if steps >= 2 * chunk and dist <= bound:
+            return steps, res, dist
+        prev = res
+    return steps, res, res * tau_slow
+
+
+def gate_study(lbm, cases, pred, bound=1e-8, storage="fp64", chunk=200, max_decay_times=60):
+    """Rest start and warm start (from the predicted profiles `pred`) of each channel on
+    its own handle, each run to a distance `bound` from the steady state (or at most
+    `max_decay_times` slowest decay times): steps, wall time and the final fields (rho, u,
+    T) of both."""
+    out = []
+    for case, pr in zip(cases, pred):
+        p = case["params"]
+        row = {}
+        for start in ("rest", "warm"):
+            sim = lbm.Simulation(storage=storage, **p)
+            if start == "rest":
+                sim.init(*sweep.initial_fields(case))
+            else:
+                lbm.lbm_init_fields_neq(sim.h, *warm_fields(case, pr))
+            tau_slow = channel_tau_slow(case, sim.r)
+            t0 = time.perf_counter()
+            steps, res, dist = run_to_steady(sim, tau_slow, bound, chunk, int(max_decay_times * tau_slow))
+            secs = time.perf_counter() - t0
+            m = sim.moments()
+            sim.close()
+            row[start] = dict(steps=steps, seconds=secs, residual=res, distance_bound=dist,
+                              fields={k: m[k] for k in ("rho", "u", "T")})
+        out.append(row)
+    return out
+
+
 def _summary(v):
     return dict(median=float(np.median(v)), p90=float(np.percentile(v, 90)), max=float(np.max(v))) if len(v) else None
 
 
 def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, max_steps=6_000_000,
-          check_every=200, train_H=(64, 128), iters=3000, refine=True):
+          check_every=200, train_H=(64, 128), iters=3000, refine=True, keep_model=False):
     """Trains on steady channels, then compares warm start and rest start on held-out
     4 x H channels: steps and batch wall time to residual `tol`, and the difference of
     the two converged states at `tol` and after both continue to `tol_fine`.  The
     residual is a per-step relative change, so a run that stops at it is still about
     tol x (slowest decay time) away from the steady state, from its own side; the
-    difference must shrink with the tolerance if both reach the same state."""
+    difference must shrink with the tolerance if both reach the same state.  With
+    keep_model the trained Surrogate is returned as res["model"]."""
     t0 = time.perf_counter()
     ts = training_set(lbm, n_train, seed, H_range=train_H, tol=tol)
     sur = Surrogate(lbm, seed=seed)
@@ -221,7 +280,8 @@ def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, 
                                                warm=float(np.median(warm9["steps"] - warm["steps"]))),
                   state_diff_at_tol_fine=dict(u=_summary(du9), T=_summary(dT9)),
                   rest_tol_state_vs_fine_u=_summary(dr8),
-                  initial_u_profile_err_median=float(np.median(perr)))), arrays
+                  initial_u_profile_err_median=float(np.median(perr))),
+        **({"model": sur} if keep_model else {})), arrays
 
 
 def main():

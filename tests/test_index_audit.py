@@ -92,3 +92,20 @@ def test_inadmissible_variants_rejected(audit):
         audit(L.LBM_D2Q37, "fp16", nx=7, variant=PAIRED)        # ... and an even row
     with pytest.raises(L.LbmError):
         audit(L.LBM_D2Q77, walls=True, ny=16)                   # no walls on D2Q77
+
+
+def test_fp64_storage_two_pass(audit):
+    # FP64 storage (8-byte values, two-pass kernel only): the byte offsets of the stores
+    # are tabulated at 8 bytes per value; the other variants are refused
+    for walls in (False, True):
+        for nx in (1, 2, 3, 4, 6, 37):
+            for ny in ((5, 6, 9) if walls else (1, 2, 3, 4, 9)):
+                assert audit(L.LBM_D2Q37, "fp64", walls, False, nx, ny, 1, TWOPASS) == 0, (walls, nx, ny)
+        for nx, ny, nz in ((1, 5, 1), (3, 7, 4), (8, 8, 8)):
+            assert audit(L.LBM_D3Q103, "fp64", walls, False, nx, ny, nz, TWOPASS) == 0, (walls, nx, ny, nz)
+    for v in (DIRECT, PAIRED, L.LBM_KERNEL_STAGED):
+        with pytest.raises(L.LbmError):
+            audit(L.LBM_D2Q37, "fp64", nx=128, variant=v)
+    with pytest.raises(L.LbmError):
+        audit(L.LBM_D2Q33, "fp64", nx=8, variant=TWOPASS)     # FP64 storage: D2Q37 and D3Q103
+

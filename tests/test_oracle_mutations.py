@@ -72,6 +72,10 @@ MUTANTS = [
      "v[d] = S->L.r * S->L.c[i][d] - st.u[d]; v2 += v[d] * v[d]; }\n                        for (int d = 0; d < D; ++d) qa[d]",
      "v[d] = S->L.r * S->L.c[i][d] + st.u[d]; v2 += v[d] * v[d]; }\n                        for (int d = 0; d < D; ++d) qa[d]",
      "tests/test_oracle_moments.py::test_heat_flux_vanishes_for_gaussians_and_pressure_is_rho_lambda"),
+    ("initial populations without the wall procedure (reading R6)",
+     "    if (S->walls) orc_walls(S, S->g, S->h);\n    S->steps = 0;",
+     "    S->steps = 0;",
+     "tests/test_oracle_transport.py::test_walls_conserve_fluid_mass_from_any_initial_state"),
     ("total energy without the 1/2 of the kinetic part (Sec. V, rho E)",
      "E += 0.5 * x2 * g + S->h[c * Q + i];",
      "E += x2 * g + S->h[c * Q + i];",

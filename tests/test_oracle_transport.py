@@ -161,6 +161,26 @@ def test_walls_conserve_fluid_mass():
     assert abs(g1 - g0) < 1e-11 * g0
 
 
+def test_walls_conserve_fluid_mass_from_any_initial_state():
+    # with the wall procedure applied to the initial populations too (reading R6), the fluid
+    # rows keep exactly the mass of the initial fields, whatever the fields on the wall
+    # rows: here a sheared, heated and compressed start whose wall rows disagree with the
+    # walls, and the mass is that of the input fields on rows 1 .. Ny-2
+    Ny, nx = 17, 3
+    rng = np.random.default_rng(9)
+    s = O.Sim(O.D2Q37, nx=nx, ny=Ny, walls=True, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8,
+              wall_u=[[0, 0, 0], [0.1, 0, 0]], wall_T=[1.0, 1.02])
+    y = np.arange(Ny)[:, None] * np.ones((1, nx))
+    rho = 1.0 + 0.03 * np.sin(np.pi * y / (Ny - 1)) + 0.01 * rng.uniform(-1, 1, (Ny, nx))
+    u = np.stack([0.08 * y / (Ny - 1), 0.01 * rng.uniform(-1, 1, (Ny, nx))])
+    T = 1.0 + 0.05 * (y / (Ny - 1)) ** 2
+    s.init(rho, u, T)
+    want = rho[1:Ny - 1].sum()
+    for steps in (0, 1, 50):
+        s.step(steps)
+        assert abs(s.populations()[0][:, 1:Ny - 1].sum() - want) < 1e-12 * want, steps
+
+
 def test_d3q103_shear_wave_viscosity():
     # the 3-D lattice (reading R4) carries the same viscosity law
     N = 32
