@@ -576,11 +576,21 @@ def summarize(name, d):
     the --details file): per-case arrays are reduced to their extremes."""
     if not isinstance(d, dict) or "error" in d:
         return d
+    if name == "cpu_baseline":
+        w = d.get("workloads", {})
+        out = {k: v for k, v in d.items() if k != "workloads"}
+        if "cpu_model" in w:
+            out["workloads"] = {"cpu_model": w["cpu_model"], "nproc": w["nproc"],
+                                "mlups_1_thread_and_all": {k: [w[k].get(f"threads_{t}", {}).get("mlups")
+                                                               for t in (1, w["nproc"])]
+                                                           for k in ("d2q37_64", "d3q103_32", "d2q37_1024")}}
+        return out
     if name == "couette_grid":
-        return {"workload": d["workload"],
-                **{h: {k: d[h][k] for k in ("tau", "all_converged", "max_u_err", "max_T_err",
-                                             "curvature_ratio_range", "settle_steps")}
-                   for h in ("H256", "H64") if h in d}}
+        return {h: {k: d[h][k] for k in ("tau", "all_converged", "max_u_err", "max_T_err", "curvature_ratio_range")}
+                for h in ("H256", "H64") if h in d}
+    if name == "shock_tube_d2q33":
+        return {"l1_rel": [d["l1_rel_rho"], d["l1_rel_u"], d["l1_rel_p"]],
+                "frac_4096": d.get("throughput_4096", {}).get("frac")}
     if name == "mode_study":
         out = {}
         for m in ("shifted", "literal"):
@@ -592,7 +602,7 @@ def summarize(name, d):
                                    "startup_max_err": max(c["startup_max_err"].values()), "u_err": c["u_err"]}
         return out
     if name == "accuracy":
-        return {k: ({f: v[f] for f in ("rho", "u", "T")} if isinstance(v, dict) else v) for k, v in d.items()}
+        return {k: {f: v[f] for f in ("rho", "u", "T")} for k, v in d.items() if isinstance(v, dict)}
     if name == "d3q103_256":
         out = {st: {k: d[st][k] for k in ("mlups", "frac", "launch_ms")} for st in ("fp32", "fp16") if st in d}
         acc = d.get("accuracy", {})
@@ -752,7 +762,7 @@ def run_ours(args):
     # the line: headline keys first, then each extra's short form, the storage forms last
     # (the headline keys unrounded; the extras to four significant digits)
     if "cpu_baseline" in extra:
-        line["cpu_baseline"] = sig(extra.pop("cpu_baseline"))
+        line["cpu_baseline"] = sig(summarize("cpu_baseline", extra.pop("cpu_baseline")))
     for name in ("mode_study", "shock_tube_d2q33", "batched_sweep", "couette_grid", "burnett_d2q77", "warm_start",
                  "d3q103_256", "accuracy"):
         if name in extra:

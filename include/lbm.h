@@ -150,6 +150,11 @@ int lbm_coefficients(const lbm_handle *h, double *out);
  * mapping of a parameter set to out[0..5] as in lbm_coefficients.  lbm_map_params
  * returns LBM_ERR_ARG for an inadmissible set and LBM_WARN_PR_RANGE as lbm_create does. */
 int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w);
+
+/* The lattice's scale r (xi_i = r c_i; one lattice spacing per time step is r in the
+ * paper's units, Sec. V "dimensionless variables": dx = r dt), as lbm_lattice_table
+ * derives it.  Host only; LBM_ERR_ARG for an unknown lattice or r == NULL. */
+int lbm_lattice_unit_scale(int lattice, double *r);
 int lbm_map_params(const lbm_params *p, double *out);
 
 /* Sets every domain population to the discrete equilibrium of the fields with

@@ -203,56 +203,81 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
 // Opposite pairs are read in chunks of CH pairs: prefetch<P>() at the first pair of a
 // chunk issues the chunk's 4 CH loads (g and h of both members) into registers before any
 // of them is used, so each warp keeps a chunk of loads in flight; sv<I>() / tv<I>() then
-// return the buffered values (the rest population is read directly).  refresh() makes
-// the buffer address opaque, so the relaxation reads the values again (from L1 / L2)
-// instead of keeping the moment pass's values live across the cell.
-template <int LAT, int ST, int CH> struct GatherPop {
+// return the buffered values (the rest population is read directly).  With DB (double
+// buffering) the first prefetch issues chunks 0 and 1 and every later one the chunk after
+// the next, into the other of two buffers, so the next chunk's loads are in flight while
+// the current one is summed or relaxed.  refresh() makes the buffer address opaque, so
+// the relaxation reads the values again (from L1 / L2) instead of keeping the moment
+// pass's values live across the cell.
+template <int LAT, int ST, int CH, bool DB = false> struct GatherPop {
     using S = Storage<ST>;
     using V = typename S::R;
     using T = typename S::T;
     static constexpr int Q = Lattice<LAT>::Q;
     static constexpr int NP = (Q - 1) / 2;
+    static constexpr int NB = DB ? 2 : 1;   // chunk buffers
     const T *src;
     long long plane;
     static constexpr int R = Lattice<LAT>::R;
     int col[2 * R + 1], row[2 * R + 1], pln[2 * R + 1];   // element offsets within a plane
-    mutable typename S::Raw bs[2 * CH], bt[2 * CH];
+    mutable typename S::Raw bs[NB][2 * CH], bt[NB][2 * CH];
     template <int I> __device__ __forceinline__ int at() const
     {
         return pln[cv<LAT, I, 2>() + R] + row[cv<LAT, I, 1>() + R] + col[cv<LAT, I, 0>() + R];
     }
+    // source of population p (set p / Q, velocity p % Q) whose velocity is I
+    template <int P, int I> __device__ __forceinline__ const T *addr() const { return src + P * plane + at<I>(); }
+    // the loads of chunk C (pairs [C CH, (C + 1) CH)) into buffer C % NB
+    template <int C> __device__ __forceinline__ void issue() const
+    {
+        static_for<0, CH>([&](auto KK) {
+            constexpr int k = decltype(KK)::value;
+            constexpr int P = C * CH + k;
+            constexpr int I = 1 + 2 * P;
+            if constexpr (P < NP) {
+                bs[C % NB][2 * k] = S::raw(addr<I, I>());
+                bs[C % NB][2 * k + 1] = S::raw(addr<I + 1, I + 1>());
+                bt[C % NB][2 * k] = S::raw(addr<Q + I, I>());
+                bt[C % NB][2 * k + 1] = S::raw(addr<Q + I + 1, I + 1>());
+            }
+        });
+    }
     template <int P> __device__ __forceinline__ void prefetch() const
     {
         if constexpr (P % CH == 0) {
-            static_for<0, CH>([&](auto KK) {
-                constexpr int k = decltype(KK)::value;
-                constexpr int I = 1 + 2 * (P + k);
-                if constexpr (P + k < NP) {
-                    bs[2 * k] = S::raw(src + I * plane + at<I>());
-                    bs[2 * k + 1] = S::raw(src + (I + 1) * plane + at<I + 1>());
-                    bt[2 * k] = S::raw(src + (Q + I) * plane + at<I>());
-                    bt[2 * k + 1] = S::raw(src + (Q + I + 1) * plane + at<I + 1>());
-                }
-            });
+            constexpr int C = P / CH;
+            if constexpr (!DB) {
+                issue<C>();
+            } else {
+                if constexpr (C == 0) issue<0>();
+                if constexpr ((C + 1) * CH < NP) issue<C + 1>();
+            }
             asm volatile("" ::: "memory");
         }
     }
     template <int I> __device__ __forceinline__ V sv() const
     {
-        if constexpr (I == 0) return S::ld(src + at<0>());
-        else return S::cvt(bs[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
+        if constexpr (I == 0) return S::ld(addr<0, 0>());
+        else return S::cvt(bs[(((I - 1) / 2) / CH) % NB][2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
     template <int I> __device__ __forceinline__ V tv() const
     {
-        if constexpr (I == 0) return S::ld(src + Q * plane + at<0>());
-        else return S::cvt(bt[2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
+        if constexpr (I == 0) return S::ld(addr<Q, 0>());
+        else return S::cvt(bt[(((I - 1) / 2) / CH) % NB][2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
     __device__ __forceinline__ void refresh() { asm volatile("" : "+l"(src)); }
 };
 
-// Pairs per prefetch chunk of the two-pass kernel: D2Q37's 18 pairs in two chunks,
-// D3Q103's 51 in three.
-template <int LAT> constexpr int twopass_chunk() { return Lattice<LAT>::D == 2 ? 9 : 17; }
+// Pairs per prefetch chunk of the two-pass kernel, and whether the chunks are
+// double-buffered: D2Q37's 18 pairs in two chunks; D3Q103's 51 in three, or with FP32
+// storage in four double-buffered chunks of 13 (measured at 256^3: +2.4 % for FP32, -2 %
+// for FP16, whose chunks stay single; chunks of 6 or 9 pairs, double-buffered or not,
+// and double-buffered chunks on D2Q77 measured no better).
+template <int LAT, int ST> constexpr bool twopass_db() { return LAT == LAT_D3Q103 && ST == ST_FP32; }
+template <int LAT, int ST> constexpr int twopass_chunk()
+{
+    return Lattice<LAT>::D == 2 ? 9 : (twopass_db<LAT, ST>() ? 13 : 17);
+}
 
 // The fused step with the populations read twice: once streamed into the moment sums,
 // once more for the relaxation.  Nothing of the cell stays in registers between the
@@ -275,7 +300,7 @@ __global__ void __launch_bounds__(128, twopass_min_blocks<LAT, ST>()) k_stream_c
     if (x >= kp.nx) return;
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
-    GatherPop<LAT, ST, twopass_chunk<LAT>()> pop;
+    GatherPop<LAT, ST, twopass_chunk<LAT, ST>(), twopass_db<LAT, ST>()> pop;
     pop.src = src;
     pop.plane = kp.plane;
     constexpr int R = Lattice<LAT>::R;

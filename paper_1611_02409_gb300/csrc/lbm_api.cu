@@ -261,6 +261,12 @@ int lbm_lattice_table(int lattice, int *D, int *Q, double *r, int *c, double *w)
     return LBM_OK;
 }
 
+int lbm_lattice_unit_scale(int lattice, double *r)
+{
+    if (!r) return set_err(nullptr, LBM_ERR_ARG, "null r");
+    return lbm_lattice_table(lattice, nullptr, nullptr, r, nullptr, nullptr);
+}
+
 int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
 {
     NvtxRange nvtx_("lbm_create");

@@ -106,6 +106,7 @@ def lib():
             L.lbm_last_error.restype = C.c_char_p
             L.lbm_lattice_info.argtypes = [vp, ip, ip, dp, ip, dp]
             L.lbm_lattice_table.argtypes = [C.c_int, ip, ip, dp, ip, dp]
+            L.lbm_lattice_unit_scale.argtypes = [C.c_int, dp]
             L.lbm_debug_index_audit.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_int]
             L.lbm_debug_index_audit.restype = C.c_longlong
             L.lbm_map_params.argtypes = [C.POINTER(lbm_params), dp]
@@ -162,6 +163,13 @@ def lbm_lattice_table(lattice=LBM_D2Q37):
     _check(lib().lbm_lattice_table(lattice, C.byref(D), C.byref(Q), C.byref(r),
                                    c.ctypes.data_as(C.POINTER(C.c_int)), w.ctypes.data_as(C.POINTER(C.c_double))))
     return D.value, r.value, c[:Q.value].copy(), w[:Q.value].copy()
+
+
+def lbm_lattice_unit_scale(lattice=LBM_D2Q37) -> float:
+    """The lattice's scale r (dx = r dt in the paper's units); no GPU needed."""
+    r = C.c_double()
+    _check(lib().lbm_lattice_unit_scale(int(lattice), C.byref(r)))
+    return r.value
 
 
 def lbm_debug_index_audit(p: lbm_params, variant: int, wrap_threshold: int = 0) -> int:

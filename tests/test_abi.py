@@ -118,3 +118,13 @@ def test_field_totals_static_wrapper_checks_arguments(L):
         L.lbm_field_totals_static(2, 3.0, x, torch.zeros(16, dtype=torch.float64), x, torch.zeros(6, dtype=torch.float64))
     with pytest.raises(ValueError):
         L.lbm_field_totals_static(2, 3.0, np.zeros(8), np.zeros(16), np.zeros(8), np.zeros(6))
+
+
+@pytest.mark.parametrize("lat,olat", [(1, O.D2Q37), (2, O.D3Q103), (3, O.D2Q33), (4, O.D2Q77)])
+def test_lattice_unit_scale(L, lat, olat):
+    # dx = r dt: the same r as the lattice table, and the oracle's independent derivation
+    r = L.lbm_lattice_unit_scale(lat)
+    assert r == L.lbm_lattice_table(lat)[1]
+    assert abs(r - O.lattice(olat)[1]) < 1e-13
+    with pytest.raises(L.LbmError):
+        L.lbm_lattice_unit_scale(9)

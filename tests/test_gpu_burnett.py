@@ -19,7 +19,8 @@ from paper_1611_02409_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 PRM = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.8)
-TOL = {"fp32": 2e-6, "fp16": 2e-3}
+# BF16: about twice the measured element-wise error (1.6e-3 after one step)
+TOL = {"fp32": 2e-6, "fp16": 2e-3, "bf16": 4e-3}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +38,7 @@ def _index(sim, o):
     return [next(j for j in range(len(o.c)) if tuple(o.c[j]) == tuple(v)) for v in sim.c]
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("kernel", [1, 4])            # direct, two-pass
 @pytest.mark.parametrize("nx,ny,open_x", [(37, 23, False), (130, 9, True), (4, 6, False), (11, 3, True),
                                           (5, 5, False)])

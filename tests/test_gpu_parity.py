@@ -11,7 +11,9 @@ Tolerances:
     as a random walk, ~6e-8 * 1e-2 * sqrt(steps) per cell, i.e. ~2e-8 after 1000 steps
     against field departures of 1e-3 (T) and 1e-2 (u): a few 1e-5 at most.
   * FP16 storage (11-bit significand, 2^-11 relative rounding of s ~ 0.01-0.3): rel <= 1e-3.
-  * BF16 storage (8-bit significand, 8x coarser): rel <= 1e-2.
+  * BF16 storage (8-bit significand, 8x coarser): it misses the 1e-3 bar (measured 1.6e-3
+    in u on the 64^2 and 128^2 Taylor-Green fields); the tests hold it to about twice the
+    measured error, rel <= 3.5e-3, so a regression shows.
 """
 import numpy as np
 import pytest
@@ -108,7 +110,7 @@ def test_populations_elementwise_ragged(L, nx, ny):
     sim.close()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 1e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 3.5e-3)])
 def test_low_precision_storage(L, storage, tol):
     fields = inputs.taylor_green_2d(64, U0=0.02, T_amp=0.01)
     mg, mo, _, _ = run_pair(L, fields, 200, storage=storage, **CFG0)
@@ -378,7 +380,7 @@ def test_staged_path_elementwise(L, nx, ny, kernel):
     sim.close()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 1e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 3.5e-3)])
 def test_staged_path_low_precision(L, storage, tol):
     fields = inputs.taylor_green_2d(128, U0=0.02, T_amp=0.01)
     mg, mo, _, _ = run_pair(L, fields, 100, storage=storage, kernel=STAGED, **CFG0)
@@ -413,7 +415,7 @@ def test_autotune_selects_a_variant_and_resets(L):
     sim.close()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 7e-3)])
 def test_interior_fast_gather_elementwise(L, storage, tol):
     # 512 x 16: blocks 1 and 2 of every row with 3 <= y < 13 gather at fixed offsets,
     # the others take the seam path; both must agree with the oracle cell by cell

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 CFG0 = dict(Pr=0.71, gamma=1.4, kappa=0.2, tau=0.528655)
 WALLS = dict(bc_y=1, wall_u=[[0, 0, 0], [0.1, 0, 0]], wall_T=[1.0, 1.02])
-TOL = {"fp32": 2e-6, "fp16": 2e-3, "bf16": 2e-2}
+# BF16: twice the largest measured element-wise error (4.6e-3, paired kernel with walls)
+TOL = {"fp32": 2e-6, "fp16": 2e-3, "bf16": 1e-2}
 
 
 @pytest.fixture(scope="module")
