@@ -209,13 +209,19 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
 // the current one is summed or relaxed.  refresh() makes the buffer address opaque, so
 // the relaxation reads the values again (from L1 / L2) instead of keeping the moment
 // pass's values live across the cell.
-template <int LAT, int ST, int CH, bool DB = false> struct GatherPop {
+template <int LAT, int ST, int CH, bool DB = false, bool PK = false> struct GatherPop {
     using S = Storage<ST>;
     using V = typename S::R;
     using T = typename S::T;
     static constexpr int Q = Lattice<LAT>::Q;
     static constexpr int NP = (Q - 1) / 2;
     static constexpr int NB = DB ? 2 : 1;   // chunk buffers
+    static_assert(!PK || (sizeof(typename S::Raw) == 2 && !DB), "packing keeps 16-bit values");
+    // PK (16-bit storage): the moment pass packs each opposite pair's two stored values into
+    // one 32-bit word that stays in registers, so the relaxation pass reads nothing again
+    mutable uint32_t wg[PK ? NP : 1], wh[PK ? NP : 1];
+    mutable typename S::Raw g0, h0;
+    bool second = false;                    // set by refresh(): the relaxation pass
     const T *src;
     long long plane;
     static constexpr int R = Lattice<LAT>::R;
@@ -246,6 +252,9 @@ template <int LAT, int ST, int CH, bool DB = false> struct GatherPop {
     {
         if constexpr (P % CH == 0) {
             constexpr int C = P / CH;
+            if constexpr (PK) {
+                if (second) return;
+            }
             if constexpr (!DB) {
                 issue<C>();
             } else {
@@ -253,19 +262,55 @@ template <int LAT, int ST, int CH, bool DB = false> struct GatherPop {
                 if constexpr ((C + 1) * CH < NP) issue<C + 1>();
             }
             asm volatile("" ::: "memory");
+            if constexpr (PK) {
+                static_for<0, CH>([&](auto KK) {
+                    constexpr int k = decltype(KK)::value;
+                    constexpr int Pk = C * CH + k;
+                    if constexpr (Pk < NP) {
+                        wg[Pk] = (uint32_t)bs[0][2 * k] | ((uint32_t)bs[0][2 * k + 1] << 16);
+                        wh[Pk] = (uint32_t)bt[0][2 * k] | ((uint32_t)bt[0][2 * k + 1] << 16);
+                    }
+                });
+            }
         }
+    }
+    // the stored value of population I of the set (g: w = wg, b = bs; h: wh, bt)
+    template <int I> __device__ __forceinline__ V packed(const uint32_t (&w)[PK ? NP : 1]) const
+    {
+        const uint32_t word = w[(I - 1) / 2];
+        return S::cvt((typename S::Raw)((I - 1) % 2 ? word >> 16 : word & 0xffffu));
     }
     template <int I> __device__ __forceinline__ V sv() const
     {
+        if constexpr (PK) {
+            if constexpr (I == 0) {
+                if (!second) g0 = S::raw(addr<0, 0>());
+                return S::cvt(g0);
+            } else if (second) {
+                return packed<I>(wg);
+            }
+        }
         if constexpr (I == 0) return S::ld(addr<0, 0>());
         else return S::cvt(bs[(((I - 1) / 2) / CH) % NB][2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
     template <int I> __device__ __forceinline__ V tv() const
     {
+        if constexpr (PK) {
+            if constexpr (I == 0) {
+                if (!second) h0 = S::raw(addr<Q, 0>());
+                return S::cvt(h0);
+            } else if (second) {
+                return packed<I>(wh);
+            }
+        }
         if constexpr (I == 0) return S::ld(addr<Q, 0>());
         else return S::cvt(bt[(((I - 1) / 2) / CH) % NB][2 * (((I - 1) / 2) % CH) + (I - 1) % 2]);
     }
-    __device__ __forceinline__ void refresh() { asm volatile("" : "+l"(src)); }
+    __device__ __forceinline__ void refresh()
+    {
+        if constexpr (PK) second = true;
+        else asm volatile("" : "+l"(src));
+    }
 };
 
 // Pairs per prefetch chunk of the two-pass kernel, and whether the chunks are
@@ -274,6 +319,12 @@ template <int LAT, int ST, int CH, bool DB = false> struct GatherPop {
 // for FP16, whose chunks stay single; chunks of 6 or 9 pairs, double-buffered or not,
 // and double-buffered chunks on D2Q77 measured no better).
 template <int LAT, int ST> constexpr bool twopass_db() { return LAT == LAT_D3Q103 && ST == ST_FP32; }
+// 16-bit storage on the large lattices: the relaxation reuses the moment pass's values,
+// packed two per register, instead of reading them again
+template <int LAT, int ST> constexpr bool twopass_pack()
+{
+    return (ST == ST_FP16 || ST == ST_BF16) && LAT == LAT_D3Q103;
+}
 template <int LAT, int ST> constexpr int twopass_chunk()
 {
     return Lattice<LAT>::D == 2 ? 9 : (twopass_db<LAT, ST>() ? 13 : 17);
@@ -287,7 +338,7 @@ template <int LAT, int ST> constexpr int twopass_chunk()
 // FP64 storage (double arithmetic, twice the registers per value): two blocks per SM.
 template <int LAT, int ST> constexpr int twopass_min_blocks()
 {
-    return ST == ST_FP64 ? 2 : (Lattice<LAT>::D == 2 ? 4 : 2);
+    return ST == ST_FP64 || twopass_pack<LAT, ST>() ? 2 : (Lattice<LAT>::D == 2 ? 4 : 2);
 }
 
 template <int LAT, int ST, bool WALLS>
@@ -300,7 +351,7 @@ __global__ void __launch_bounds__(128, twopass_min_blocks<LAT, ST>()) k_stream_c
     if (x >= kp.nx) return;
     const int y = blockIdx.y + kp.y0;
     const int z = blockIdx.z;
-    GatherPop<LAT, ST, twopass_chunk<LAT, ST>(), twopass_db<LAT, ST>()> pop;
+    GatherPop<LAT, ST, twopass_chunk<LAT, ST>(), twopass_db<LAT, ST>(), twopass_pack<LAT, ST>()> pop;
     pop.src = src;
     pop.plane = kp.plane;
     constexpr int R = Lattice<LAT>::R;
