@@ -115,16 +115,23 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 }
 
 // ---- tcgen05 form -------------------------------------------------------------------
-// One CTA (4 warps) computes a TM x TN tile of C.  Per K step of TK, the threads stage
+// One CTA (4 warps) computes a TM x TN tile of C (TN = 64, or 32 when 64-wide tiles would
+// leave most SMs idle).  Per K step of TK, the threads stage
 // op(A) (TM x TK) and op(B) (as TN rows of TK) in shared memory in the canonical
 // no-swizzle K-major layout: 8-row x 16-byte core matrices, row group by row group, so
 // K-adjacent core matrices are 128 bytes apart (the descriptors' leading byte offset) and
-// 8-row groups TK / 8 x 128 bytes apart (the stride byte offset).  One thread issues the
-// TK / 16 MMAs (M = 128, N = 64, K = 16, BF16 x BF16 -> FP32 in tensor memory) and commits
-// them to an mbarrier; every thread waits (bounded: on timeout the kernel sets *err and
-// leaves C unwritten) before the tiles are restaged.  The epilogue reads each thread's row
-// (TMEM lane) with tcgen05.ld and applies bias, GELU and the bfloat16 copy as k_gemm does.
-constexpr int TM = 128, TN = 64, TK = 64;
+// 8-row groups TK / 8 x 128 bytes apart (the stride byte offset).  Staging moves 16-byte
+// groups of eight values: eight consecutive k of one row when the operand is contiguous
+// in k (one 16-byte load, one 16-byte store into its core-matrix row), eight consecutive
+// rows at one k otherwise (one 16-byte load, eight 2-byte stores); groups that cross the
+// matrix edge or an unaligned address are read element by element, zero outside.  Every
+// thread holds its groups of the next K step in registers, loaded while the MMAs of the
+// current step run.  One thread issues the TK / 16 MMAs (M = 128, N = 64, K = 16, BF16 x
+// BF16 -> FP32 in tensor memory) and commits them to an mbarrier; every thread waits
+// (bounded: on timeout the kernel sets *err and leaves C unwritten) before the tiles are
+// restaged.  The epilogue reads each thread's row (TMEM lane) with tcgen05.ld and applies
+// bias, GELU and the bfloat16 copy as k_gemm does.
+constexpr int TM = 128, TK = 64;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -145,6 +152,59 @@ __device__ __forceinline__ uint64_t mma_sdesc(uint32_t addr)
     return d;
 }
 
+// Group g (0 <= g < ROWS TK / 8) of an operand for the K step at k0: its tile row r and
+// first k (kmaj: eight consecutive k of row r; else eight consecutive rows from r at k),
+// loaded from X (op(X)[r][k] = kmaj ? X[r ld + k] : X[k ld + r]; rows below rlim, k
+// below klim; zero outside).
+template <int ROWS> struct StageGroup {
+    static __device__ __forceinline__ void place(int g, bool kmaj, int &r, int &k)
+    {
+        if (kmaj) {
+            r = g / (TK / 8);
+            k = (g % (TK / 8)) * 8;
+        } else {
+            k = g / (ROWS / 8);
+            r = (g % (ROWS / 8)) * 8;
+        }
+    }
+    static __device__ __forceinline__ uint4 load(const bf16 *__restrict__ X, int ld, bool kmaj, int r0, int rlim,
+                                                 int k0, int klim, int g)
+    {
+        int r, k;
+        place(g, kmaj, r, k);
+        const int gr = r0 + r, gk = k0 + k;
+        const bf16 *p = kmaj ? X + (long long)gr * ld + gk : X + (long long)gk * ld + gr;
+        const bool full = kmaj ? (gr < rlim && gk + 8 <= klim) : (gk < klim && gr + 8 <= rlim);
+        if (full && (reinterpret_cast<uintptr_t>(p) & 15) == 0) return __ldg(reinterpret_cast<const uint4 *>(p));
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            unsigned short e[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const bool in = kmaj ? (gr < rlim && gk + j + i < klim) : (gk < klim && gr + j + i < rlim);
+                e[i] = in ? __bfloat16_as_ushort(p[kmaj ? j + i : (long long)(j + i)]) : (unsigned short)0;
+            }
+            w[j / 2] = (uint32_t)e[0] | ((uint32_t)e[1] << 16);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    static __device__ __forceinline__ void store(unsigned char *s, bool kmaj, int g, uint4 v)
+    {
+        int r, k;
+        place(g, kmaj, r, k);
+        if (kmaj) {
+            *reinterpret_cast<uint4 *>(s + core_off(r, k)) = v;
+        } else {
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<unsigned short *>(s + core_off(r + j, k)) =
+                    (unsigned short)(j & 1 ? w[j / 2] >> 16 : w[j / 2] & 0xffffu);
+        }
+    }
+};
+
 __device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity)
 {
     const long long t0 = clock64();
@@ -160,6 +220,7 @@ __device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity)
     }
 }
 
+template <int TN>
 __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, int lda, int ta,
                                                  const bf16 *__restrict__ B, int ldb, int tb, float *C, int ldc,
                                                  const float *__restrict__ bias, int act, float *Cpre, bf16 *Cbf,
@@ -187,21 +248,22 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
     // instruction descriptor: D FP32, A and B BF16, both K-major, N / 8, M / 16
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
-    const bf16 zero = __float2bfloat16(0.f);
     uint32_t phase = 0;
     int ok = 1;
+    // op(A) rows are m (contiguous in k unless ta); op(B) rows are n (contiguous in k if tb).
+    // Group g of a thread: tid + 128 j, so consecutive threads read consecutive addresses.
+    constexpr int GA = TM * TK / 8 / 128, GB = TN * TK / 8 / 128;
+    const bool akm = !ta, bkm = tb != 0;
+    uint4 va[GA], vb[GB];
+#pragma unroll
+    for (int j = 0; j < GA; ++j) va[j] = StageGroup<TM>::load(A, lda, akm, m0, M, 0, K, tid + 128 * j);
+#pragma unroll
+    for (int j = 0; j < GB; ++j) vb[j] = StageGroup<TN>::load(B, ldb, bkm, n0, N, 0, K, tid + 128 * j);
     for (int k0 = 0; k0 < K; k0 += TK) {
-        // consecutive threads take consecutive global addresses of each operand
-        for (int e = tid; e < TM * TK; e += 128) {
-            const int r = ta ? e % TM : e / TK, k = ta ? e / TM : e % TK, gm = m0 + r, gk = k0 + k;
-            const bf16 v = (gm < M && gk < K) ? (ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : zero;
-            *reinterpret_cast<bf16 *>(sA + core_off(r, k)) = v;
-        }
-        for (int e = tid; e < TN * TK; e += 128) {
-            const int r = tb ? e / TK : e % TN, k = tb ? e % TK : e / TN, gn = n0 + r, gk = k0 + k;
-            const bf16 v = (gn < N && gk < K) ? (tb ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn]) : zero;
-            *reinterpret_cast<bf16 *>(sB + core_off(r, k)) = v;
-        }
+#pragma unroll
+        for (int j = 0; j < GA; ++j) StageGroup<TM>::store(sA, akm, tid + 128 * j, va[j]);
+#pragma unroll
+        for (int j = 0; j < GB; ++j) StageGroup<TN>::store(sB, bkm, tid + 128 * j, vb[j]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -217,6 +279,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_addr(&bar))
                          : "memory");
+        }
+        // the next K step's groups load while the MMAs run
+        if (k0 + TK < K) {
+#pragma unroll
+            for (int j = 0; j < GA; ++j) va[j] = StageGroup<TM>::load(A, lda, akm, m0, M, k0 + TK, K, tid + 128 * j);
+#pragma unroll
+            for (int j = 0; j < GB; ++j) vb[j] = StageGroup<TN>::load(B, ldb, bkm, n0, N, k0 + TK, K, tid + 128 * j);
         }
         const int w = mbar_wait_limit(&bar, phase) ? 1 : 0;
         phase ^= 1;
@@ -342,6 +411,7 @@ struct lbm_mlp {
     double *partials = nullptr, *dloss = nullptr;
     int *err = nullptr;             // set by a tcgen05 GEMM whose MMA wait timed out
     int gemm_kind = LBM_MLP_GEMM_TCGEN05;
+    int num_sms = 1;                // of the device the handle was created on
     int batch = 0;
     long long t = 0;
     cudaStream_t stream = nullptr;
@@ -361,8 +431,17 @@ void gemm(lbm_mlp *h, int M, int N, int K, const bf16 *A, int lda, int ta, const
           int ldc, const float *bias, int act, float *Cpre, bf16 *Cbf)
 {
     if (h->gemm_kind == LBM_MLP_GEMM_TCGEN05) {
-        dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-        k_gemm_tc<<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf, h->err);
+        // 64-wide tiles unless they would occupy fewer than half of the SMs
+    const int tiles64 = ((N + 63) / 64) * ((M + TM - 1) / TM);
+    if (tiles64 < h->num_sms / 2) {
+        dim3 grid((N + 31) / 32, (M + TM - 1) / TM);
+        k_gemm_tc<32><<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf,
+                                                  h->err);
+        return;
+    }
+    dim3 grid((N + 63) / 64, (M + TM - 1) / TM);
+        k_gemm_tc<64><<<grid, 128, 0, h->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, bias, act, Cpre, Cbf,
+                                                  h->err);
         return;
     }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
@@ -396,6 +475,12 @@ int lbm_mlp_create(int nlayers, const int *sizes, int max_batch, void *stream, l
     h->maxb = max_batch;
     h->sizes.assign(sizes, sizes + nlayers + 1);
     h->stream = (cudaStream_t)stream;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->num_sms < 1) h->num_sms = 1;
+    }
     int maxn = 0;
     for (int l = 0; l < nlayers; ++l) {
         h->woff.push_back(h->nparam);

@@ -284,6 +284,35 @@ def study(lbm, n_train=256, n_test=256, H=256, seed=0, tol=1e-8, tol_fine=1e-9, 
         **({"model": sur} if keep_model else {})), arrays
 
 
+def time_training(lbm, batch=256, iters=50, sizes=SIZES, seed=0):
+    """Milliseconds per training iteration (forward, backward with the loss, Adam) of the
+    network on random data, for each matrix-product form (tcgen05, mma.sync)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = torch.tensor(rng.uniform(-1, 1, (batch, sizes[0])), dtype=torch.float32, device="cuda")
+    y = torch.tensor(rng.normal(size=(batch, sizes[-1])), dtype=torch.float32, device="cuda")
+    out = {}
+    for name, kind in (("tcgen05", lbm.LBM_MLP_GEMM_TCGEN05), ("mma_sync", lbm.LBM_MLP_GEMM_MMA_SYNC)):
+        net = lbm.MLP(sizes, max_batch=batch, gemm=kind)
+        net.set_params(glorot(sizes, seed))
+        for _ in range(3):
+            net.forward(x)
+            net.backward(y, want_loss=False)
+            net.adam(lr=1e-3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(net.stream)
+        for _ in range(iters):
+            net.forward(x)
+            net.backward(y, want_loss=False)
+            net.adam(lr=1e-3)
+        e1.record(net.stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / iters
+        net.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n-train", type=int, default=256)
@@ -293,9 +322,14 @@ def main():
     ap.add_argument("--max-steps", type=int, default=6_000_000)
     ap.add_argument("--out", default=None)
     ap.add_argument("--npz", default=None, help="per-channel steps and state differences")
+    ap.add_argument("--time-training", action="store_true",
+                    help="only time training iterations of the network (batch 256, random data)")
     a = ap.parse_args()
     from . import build, lbm
     build.build()
+    if a.time_training:
+        print(json.dumps({"ms_per_iteration": time_training(lbm), "batch": 256, "sizes": SIZES}))
+        return
     res, arrays = study(lbm, a.n_train, a.n_test, a.H, iters=a.iters, max_steps=a.max_steps)
     s = json.dumps(res, indent=1, default=float)
     print(s)

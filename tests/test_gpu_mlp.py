@@ -35,10 +35,12 @@ GEMMS = [0, 1]  # LBM_MLP_GEMM_TCGEN05, LBM_MLP_GEMM_MMA_SYNC
 
 @pytest.mark.parametrize("gemm", GEMMS)
 @pytest.mark.parametrize("sizes,batch", [([5, 64, 48, 40], 37), ([5, 512, 512, 512, 512, 1024], 256),
-                                         ([5, 200, 130, 72], 300)])
+                                         ([5, 200, 130, 72], 300), ([5, 1024, 1024], 1100)])
 def test_forward_and_gradients_match_reference(L, sizes, batch, gemm):
-    # the last case is ragged in every product dimension against the 128 x 64 tcgen05
-    # tiles and their 64-wide K steps (batch 300 = 2 x 128 + 44; widths 200, 130, 72)
+    # the third case is ragged in every product dimension against the 128-row tcgen05
+    # tiles and their 64-wide K steps (batch 300 = 2 x 128 + 44; widths 200, 130, 72); the
+    # products of the small cases run on 32-wide tiles (64-wide ones would leave most SMs
+    # idle), the 1100 x 1024 x 1024 ones of the last case on 64-wide tiles
     import torch
     rng = np.random.default_rng(5)
     params = M.init_params(sizes, seed=11)
