@@ -88,8 +88,8 @@ extern "C" {
 
 /* stream-collide kernel variants (lbm_set_kernel / lbm_autotune) */
 #define LBM_KERNEL_AUTO 0    /* the library's default for the configuration: PAIRED
-                                where admissible, TWOPASS on D3Q103 and D2Q77, else
-                                DIRECT                                                 */
+                                where admissible, TWOPASS on D3Q103, D2Q77 and with
+                                FP64 storage, else DIRECT                              */
 #define LBM_KERNEL_DIRECT 1  /* one cell per thread, populations gathered from HBM     */
 #define LBM_KERNEL_STAGED 2  /* persistent tiles staged in shared memory by bulk
                                 asynchronous copies (D2Q37, periodic x, nx a multiple
@@ -97,8 +97,9 @@ extern "C" {
 #define LBM_KERNEL_PAIRED 3  /* two neighbouring cells per thread in packed FP32 pairs
                                 (D2Q37, FP16 or BF16 storage, periodic x, nx even)     */
 #define LBM_KERNEL_TWOPASS 4 /* one cell per thread, populations read twice (moments,
-                                then relaxation) instead of held in registers; every
-                                lattice                                                */
+                                then relaxation) instead of held in registers (16-bit
+                                storage on D3Q103: kept packed between the passes);
+                                every lattice, the only form for FP64 storage          */
 
 /* memory space of field pointers */
 #define LBM_MEM_DEVICE 0
@@ -174,6 +175,17 @@ int lbm_init_fields(lbm_handle *h, const double *rho, const double *u, const dou
  * through the first of h. */
 int lbm_init_fields_neq(lbm_handle *h, const double *rho, const double *u, const double *T, const double *Pi,
                         const double *q, int mem);
+
+/* lbm_init_fields_neq with fields of either precision: dtype LBM_DTYPE_F64 (double
+ * arrays, exactly lbm_init_fields_neq) or LBM_DTYPE_F32 (float arrays, widened to FP64
+ * first: on the host for LBM_MEM_HOST, by a kernel on the handle's stream into the
+ * handle's staging buffer for LBM_MEM_DEVICE).  Pi and q may be NULL (equilibrium only, as
+ * lbm_init_fields).  No paper counterpart: a convenience of the interface.  LBM_ERR_ARG for
+ * a null field, an unknown dtype or mem; LBM_ERR_NOMEM if the staging buffer cannot grow. */
+#define LBM_DTYPE_F64 0
+#define LBM_DTYPE_F32 1
+int lbm_init_fields_typed(lbm_handle *h, const void *rho, const void *u, const void *T, const void *Pi,
+                          const void *q, int dtype, int mem);
 
 /* Queues nsteps fused pull-stream + collide steps (+ the wall kernel when bc_y is
  * LBM_WALLS) on the handle's stream.  nsteps >= 0. */

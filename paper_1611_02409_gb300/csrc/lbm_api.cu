@@ -2,10 +2,12 @@
 // buffers, and the host side of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "kernels.cuh"
@@ -462,6 +464,62 @@ int lbm_init_fields_neq(lbm_handle *h, const double *rho, const double *u, const
     h->steps = 0;
     h->have_snap = 0;
     return LBM_OK;
+}
+
+} // extern "C"
+
+namespace {
+// FP32 fields widened to the FP64 the initialisation takes.
+__global__ void k_widen(const float *__restrict__ s, double *__restrict__ d, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = (double)s[i];
+}
+} // namespace
+
+extern "C" {
+
+int lbm_init_fields_typed(lbm_handle *h, const void *rho, const void *u, const void *T, const void *Pi,
+                          const void *q, int dtype, int mem)
+{
+    if (!h || !rho || !u || !T) return set_err(h, LBM_ERR_ARG, "null field");
+    if (dtype == LBM_DTYPE_F64)
+        return lbm_init_fields_neq(h, (const double *)rho, (const double *)u, (const double *)T, (const double *)Pi,
+                                   (const double *)q, mem);
+    if (dtype != LBM_DTYPE_F32) return set_err(h, LBM_ERR_ARG, "bad dtype");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return set_err(h, LBM_ERR_ARG, "bad mem");
+    const long long n = ncell(h);
+    const int D = h->D, np = D * (D + 1) / 2;
+    const void *in[5] = {rho, u, T, Pi, q};
+    const long long cnt[5] = {n, D * n, n, np * n, D * n};
+    long long off[5], total = 0;
+    for (int k = 0; k < 5; ++k) {
+        off[k] = total;
+        if (in[k]) total += cnt[k];
+    }
+    const double *out[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (mem == LBM_MEM_HOST) {
+        std::vector<double> wide((size_t)total);
+        for (int k = 0; k < 5; ++k) {
+            if (!in[k]) continue;
+            const float *s = static_cast<const float *>(in[k]);
+            for (long long i = 0; i < cnt[k]; ++i) wide[(size_t)(off[k] + i)] = (double)s[i];
+            out[k] = wide.data() + off[k];
+        }
+        // pageable host memory: the staged copies have left `wide` when the call returns
+        return lbm_init_fields_neq(h, out[0], out[1], out[2], out[3], out[4], LBM_MEM_HOST);
+    }
+    int rc = ensure_stage(h, sizeof(double) * (size_t)total);
+    if (rc) return rc;
+    for (int k = 0; k < 5; ++k) {
+        if (!in[k]) continue;
+        double *d = h->d_stage + off[k];
+        const int blocks = (int)std::min<long long>((cnt[k] + 255) / 256, 4096);
+        k_widen<<<blocks, 256, 0, h->stream>>>(static_cast<const float *>(in[k]), d, cnt[k]);
+        out[k] = d;
+    }
+    LBM_CK(h, cudaGetLastError());
+    return lbm_init_fields_neq(h, out[0], out[1], out[2], out[3], out[4], LBM_MEM_DEVICE);
 }
 
 int lbm_step(lbm_handle *h, int nsteps)

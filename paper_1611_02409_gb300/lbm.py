@@ -113,6 +113,7 @@ def lib():
             L.lbm_coefficients.argtypes = [vp, dp]
             L.lbm_init_fields.argtypes = [vp, vp, vp, vp, C.c_int]
             L.lbm_init_fields_neq.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
+            L.lbm_init_fields_typed.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, C.c_int]
             L.lbm_batch_init_fields_neq.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]
             L.lbm_step.argtypes = [vp, C.c_int]
             L.lbm_moments.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int]
@@ -231,6 +232,42 @@ def lbm_init_fields(h, rho, u, T):
 def lbm_init_fields_neq(h, rho, u, T, Pi=None, q=None):
     mem = _mem_of(*[x for x in (rho, u, T, Pi, q) if x is not None])
     return _check(lib().lbm_init_fields_neq(h, *(_ptr(x)[0] for x in (rho, u, T, Pi, q)), mem), h)
+
+
+LBM_DTYPE_F64 = 0
+LBM_DTYPE_F32 = 1
+
+
+def lbm_init_fields_typed(h, rho, u, T, Pi=None, q=None):
+    """lbm_init_fields_neq with FP32 or FP64 fields (all of one dtype and one memory space:
+    torch tensors on the device or host numpy arrays, contiguous)."""
+    xs = [x for x in (rho, u, T, Pi, q) if x is not None]
+    names = {str(x.dtype).replace("torch.", "") for x in xs}
+    if names == {"float64"}:
+        dtype = LBM_DTYPE_F64
+    elif names == {"float32"}:
+        dtype = LBM_DTYPE_F32
+    else:
+        raise ValueError(f"fields must all be float32 or all float64, got {sorted(names)}")
+    mems = set()
+    ptrs = []
+    for x in (rho, u, T, Pi, q):
+        if x is None:
+            ptrs.append(None)
+            continue
+        if hasattr(x, "data_ptr"):
+            if not x.is_contiguous():
+                raise ValueError("fields must be contiguous")
+            ptrs.append(C.c_void_p(x.data_ptr()))
+            mems.add(LBM_MEM_DEVICE if x.is_cuda else LBM_MEM_HOST)
+        else:
+            if not x.flags.c_contiguous:
+                raise ValueError("fields must be contiguous")
+            ptrs.append(C.c_void_p(x.ctypes.data))
+            mems.add(LBM_MEM_HOST)
+    if len(mems) != 1:
+        raise ValueError("all fields must live in the same memory space")
+    return _check(lib().lbm_init_fields_typed(h, *ptrs, dtype, mems.pop()), h)
 
 
 def lbm_step(h, nsteps=1):

@@ -128,3 +128,7 @@ def test_lattice_unit_scale(L, lat, olat):
     assert abs(r - O.lattice(olat)[1]) < 1e-13
     with pytest.raises(L.LbmError):
         L.lbm_lattice_unit_scale(9)
+
+
+def test_typed_init_refuses_a_null_handle(L):
+    assert L.lib().lbm_init_fields_typed(None, None, None, None, None, None, 1, 1) == L.LBM_ERR_ARG
