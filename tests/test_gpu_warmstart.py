@@ -39,21 +39,24 @@ def test_init_neq_reproduces_stress_and_heat_flux(L):
 
 
 def test_surrogate_warm_start_saves_steps(L):
-    # Steps to residual 1e-9 (per-step relative change of u_x and T) from rest and from
+    # Steps to residual 1e-8 (per-step relative change of u_x and T) from rest and from
     # the surrogate; then both are run well past convergence and must end in the same
-    # steady state.  In FP32 the discrete dynamics come to rest at fixed points that
-    # depend on the path by some tens of ulps of the stored deviations (measured 1-3e-6
-    # relative on u for these channels), so the bar is 1e-5.
+    # steady state.  In FP32 the per-step change of these channels bottoms out at
+    # 0.5-2e-9 (measured every 200 steps up to 12000 steps from rest), so a 1e-9 stop is
+    # reached at random times once the fields have settled; 1e-8 lies above that floor.
+    # The FP32 dynamics come to rest at fixed points that depend on the path by some
+    # tens of ulps of the stored deviations (measured 1-3e-6 relative on u for these
+    # channels), so the bar is 1e-5.
     from paper_1611_02409_gb300 import surrogate as S
     from paper_1611_02409_gb300 import sweep
-    ts = S.training_set(L, n=24, seed=3, H_range=(13, 21), tol=1e-9, max_steps=400000, check_every=100)
+    ts = S.training_set(L, n=24, seed=3, H_range=(13, 21), tol=1e-8, max_steps=400000, check_every=100)
     assert ts["converged"].all()
     sur = S.Surrogate(L, seed=0, max_batch=64, sizes=[5, 128, 128, 4 * S.NPTS])
     losses = sur.fit(ts["X"], ts["Y"], iters=800, lr=2e-3, log_every=200)
     assert losses[-1][1] < 0.2 * losses[0][1]
     test = S.draw_channels(6, seed=77, H=17)
     pred = sur.predict(np.array([c["inputs"] for c in test]))
-    tol = 1e-9
+    tol = 1e-8
     rest, _, br = S.run_channels(L, test, lambda i, bt: bt.init(i, *sweep.initial_fields(test[i])), tol, 400000,
                                  100)
     warm, _, bw = S.run_channels(L, test, lambda i, bt: bt.init_neq(i, *S.warm_fields(test[i], pred[i])), tol,
