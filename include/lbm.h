@@ -121,6 +121,13 @@ typedef struct lbm_params {
     double wall_u[2][3];  /* bottom (y = 0) / top (y = ny-1) wall velocity (tangential x)   */
     double wall_T[2];     /* bottom / top wall temperature, > 0                            */
     int bc_x;             /* LBM_PERIODIC (default, 0) or LBM_OPEN (D = 2)                 */
+    double rho0, T0;      /* reference state of the stored populations, > 0 (0 reads as 1):
+                             the library stores each population less the rest equilibrium
+                             at (rho0, u = 0, T0), scaled by its weight.  Only the rounding
+                             of the stored values depends on it (16-bit storage keeps its
+                             relative precision on flows whose mean state is far from
+                             rho = T = 1); the scheme, its lattice (Gauss-Hermite at unit
+                             temperature, Sec. III) and every input and output are the same */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;
@@ -262,7 +269,9 @@ int lbm_field_totals_static(int D, double N_f, long long n, const double *rho, c
                             double *out, void *stream);
 
 /* Checkpoint / resume: copies the domain populations (not ghost rows) as FP64 absolute
- * values g[Q][n], h[Q][n] (host or device per `mem`) out of / into the handle. */
+ * values g[Q][n], h[Q][n] (host or device per `mem`) out of / into the handle.  The
+ * reference state's shift is added / removed in FP64, so the values do not depend on it
+ * beyond the rounding of the storage form. */
 int lbm_get_populations(lbm_handle *h, double *g, double *hh, int mem);
 int lbm_set_populations(lbm_handle *h, const double *g, const double *hh, int mem);
 

@@ -61,37 +61,54 @@ template <int ELEM> struct StrideOff {
     __device__ __forceinline__ long long operator()(int I) const { return (long long)(I * plane) * ELEM; }
 };
 
-// Relax population I of a cell and store it: s' = s + omega(G~/w - s), same for t.
+// Relax population I of a cell and store it: s' = s + omega(G~/w - dg - s), same for t
+// with dh (dg, dh: the reference state's shift of velocity I's shell, see shift_g/shift_h).
 // `cell` is the destination cell's address in set 0 plane 0; off(I) the planes' byte offsets.
 // With V = f2 (two neighbouring cells, 16-bit storage) both lanes are relaxed by packed
 // FMAs and stored as one 32-bit word at the first cell's address.
-template <int LAT, int ST, class Off, class V, class S>
+// SHIFT = false (the kernels of a handle without a reference state) drops dg, dh.
+template <int LAT, int ST, bool SHIFT = true, class Off, class V, class S>
 __device__ __forceinline__ void relax_store(typename Storage<ST>::T *__restrict__ cell, const Off &off, int I,
-                                            S om, const EqScalT<V> &z, V q, V s, V t)
+                                            S om, const EqScalT<V> &z, V q, V s, V t, S dg, S dh)
 {
     using T = typename Storage<ST>::T;
     constexpr int Q = Lattice<LAT>::Q;
     char *b = reinterpret_cast<char *>(cell);
     if constexpr (std::is_same<V, f2>::value) {
         static_assert(ST != ST_FP32, "paired cells use 16-bit storage");
-        Storage<ST>::st2(reinterpret_cast<T *>(b + off(I)), vfma(f2(z.om1), s, vfma(f2(om), q, z.wdrho)));
-        Storage<ST>::st2(reinterpret_cast<T *>(b + off(Q + I)), vfma(f2(z.om1), t, vfma(z.whr, q, z.whb)));
+        const f2 wg = SHIFT ? z.wdrho - f2(dg) : z.wdrho, wh = SHIFT ? z.whb - f2(dh) : z.whb;
+        Storage<ST>::st2(reinterpret_cast<T *>(b + off(I)), vfma(f2(z.om1), s, vfma(f2(om), q, wg)));
+        Storage<ST>::st2(reinterpret_cast<T *>(b + off(Q + I)), vfma(f2(z.om1), t, vfma(z.whr, q, wh)));
     } else if constexpr (ST == ST_FP32 || ST == ST_FP64) {
         // difference form: the non-equilibrium part G~/w - s is formed exactly
-        const V Gs = z.drho + q;
-        const V Ht = vfma(z.hr, q, z.hb);
+        const V Gs = SHIFT ? (z.drho + q) - dg : z.drho + q;
+        const V Ht = SHIFT ? vfma(z.hr, q, z.hb) - dh : vfma(z.hr, q, z.hb);
         Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), vfma(om, Gs - s, s));
         Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), vfma(om, Ht - t, t));
     } else {
         // (1 - omega) s + omega G~/w in two FMAs (z carries omega-scaled terms); its extra
         // FP32 rounding is far below the 16-bit storage rounding
-        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), fmaf(z.om1, s, fmaf(om, q, z.wdrho)));
-        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), fmaf(z.om1, t, fmaf(z.whr, q, z.whb)));
+        const float wg = SHIFT ? z.wdrho - dg : z.wdrho, wh = SHIFT ? z.whb - dh : z.whb;
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(I)), fmaf(z.om1, s, fmaf(om, q, wg)));
+        Storage<ST>::st(reinterpret_cast<T *>(b + off(Q + I)), fmaf(z.om1, t, fmaf(z.whr, q, wh)));
     }
 }
 
+// The reference state's shift of the relaxation target for shell `sh`, in the form
+// relax_store takes: omega-scaled for 16-bit storage.
+template <int ST, int LAT, class S> __device__ __forceinline__ S shift_g(const KParams<LAT, S> &kp, int sh)
+{
+    return (ST == ST_FP16 || ST == ST_BF16) ? kp.ref_wg[sh] : kp.ref_g[sh];
+}
+template <int ST, int LAT, class S> __device__ __forceinline__ S shift_h(const KParams<LAT, S> &kp, int sh)
+{
+    return (ST == ST_FP16 || ST == ST_BF16) ? kp.ref_wh[sh] : kp.ref_h[sh];
+}
+
 // Collide one cell's streamed populations (accessor `pop`) and store them at offset o.
-template <int LAT, int ST, class Pop, class Off = TableOff, class S = float>
+// REF: the handle has a reference state (rho0, T0) != (1, 1); without one the kernels
+// compile without the reference's moment share and relaxation shifts.
+template <int LAT, int ST, bool REF = true, class Pop, class Off = TableOff, class S = float>
 __device__ __forceinline__ void collide_store(const KParams<LAT, S> &kp, const Pop &pop,
                                               typename Storage<ST>::T *__restrict__ dst, long long o,
                                               const Off &off = Off{nullptr})
@@ -102,14 +119,15 @@ __device__ __forceinline__ void collide_store(const KParams<LAT, S> &kp, const P
     using V = typename Pop::V;
     RawMoments<D, V> m;
     raw_moments<LAT, PRECISE>(kp, pop, m);
+    if constexpr (REF) add_reference(kp, m);
     CellState<D, V> c;
     // packed lanes (16-bit storage) divide with the fast reciprocal; one-cell lanes keep
     // IEEE division (on the 3-D two-pass kernel the fast form costs registers and spills)
-    cell_state<LAT, std::is_same<V, f2>::value>(kp, m, c);
+    cell_state<LAT, std::is_same<V, f2>::value, PRECISE && REF>(kp, m, c);
     EqState<D, V> e;
     es_state<LAT>(kp, c, e);
     PolyCoef<D, V, Lattice<LAT>::ORDER> pc;
-    poly_coeffs<D>(e, kp.r, kp.R2_hi, PRECISE ? kp.R2_lo : 0.f, pc);
+    poly_coeffs<PRECISE, REF>(e, kp, pc);
     EqScalT<V> z = eq_scalars<D>(e, kp.halfNf);
     z.om1 = 1.f - kp.omega;
     z.wdrho = kp.omega * z.drho;
@@ -120,15 +138,19 @@ __device__ __forceinline__ void collide_store(const KParams<LAT, S> &kp, const P
     if constexpr (std::is_same<Off, TableOff>::value) so.soff = kp.soff;
     Pop rp = pop;
     rp.refresh();
-    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], rp.template sv<0>(), rp.template tv<0>());
+    relax_store<LAT, ST, REF>(cell, so, 0, kp.omega, z, pc.k[0], rp.template sv<0>(), rp.template tv<0>(),
+                              shift_g<ST>(kp, 0), shift_h<ST>(kp, 0));
     static_for<0, (Q - 1) / 2>([&](auto PP) {
         constexpr int I = 1 + 2 * decltype(PP)::value;
+        constexpr int sh = Lattice<LAT>::T.shell[I];
         rp.template prefetch<decltype(PP)::value>();
         V E, O;
         poly_eval_pair<LAT, I>(pc, E, O);
-        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, rp.template sv<I>(), rp.template tv<I>());
-        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, rp.template sv<I + 1>(),
-                             rp.template tv<I + 1>());
+        const S dg = shift_g<ST>(kp, sh), dh = shift_h<ST>(kp, sh);
+        relax_store<LAT, ST, REF>(cell, so, I, kp.omega, z, E + O, rp.template sv<I>(), rp.template tv<I>(), dg,
+                                  dh);
+        relax_store<LAT, ST, REF>(cell, so, I + 1, kp.omega, z, E - O, rp.template sv<I + 1>(),
+                                  rp.template tv<I + 1>(), dg, dh);
     });
 }
 
@@ -140,7 +162,7 @@ __device__ __forceinline__ void collide_store(const KParams<LAT, S> &kp, const P
 // loads in flight for FP32 and better latency hiding for the compute-bound 16-bit forms.
 template <int LAT, int ST> constexpr int direct_min_blocks() { return Lattice<LAT>::D == 2 ? 4 : 1; }
 
-template <int LAT, int ST, bool WALLS>
+template <int LAT, int ST, bool WALLS, bool REF>
 __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_collide(const typename Storage<ST>::T *__restrict__ src,
                                                         typename Storage<ST>::T *__restrict__ dst,
                                                         const KParamsOf<LAT, ST> kp, int small_x, int small_y,
@@ -194,7 +216,7 @@ __global__ void __launch_bounds__(128, direct_min_blocks<LAT, ST>()) k_stream_co
         s[i] = S::cvt(rs[i]);
         t[i] = S::cvt(rt[i]);
     }
-    collide_store<LAT, ST>(kp, ArrayPopT<typename S::R>{s, t}, dst, o);
+    collide_store<LAT, ST, REF>(kp, ArrayPopT<typename S::R>{s, t}, dst, o);
 }
 
 // Populations read from the source buffer where they are used (two-pass kernel): a cell's
@@ -341,7 +363,7 @@ template <int LAT, int ST> constexpr int twopass_min_blocks()
     return ST == ST_FP64 || twopass_pack<LAT, ST>() ? 2 : (Lattice<LAT>::D == 2 ? 4 : 2);
 }
 
-template <int LAT, int ST, bool WALLS>
+template <int LAT, int ST, bool WALLS, bool REF>
 __global__ void __launch_bounds__(128, twopass_min_blocks<LAT, ST>()) k_stream_collide_2p(
     const typename Storage<ST>::T *__restrict__ src, typename Storage<ST>::T *__restrict__ dst,
     const KParamsOf<LAT, ST> kp, int small_x, int small_y, int small_z)
@@ -365,7 +387,7 @@ __global__ void __launch_bounds__(128, twopass_min_blocks<LAT, ST>()) k_stream_c
         if constexpr (D == 3) pop.pln[KK] = wrap_sub<C>(z, kp.nz, small_z) * kp.nys * kp.nx;
         else pop.pln[KK] = 0;
     });
-    collide_store<LAT, ST>(kp, pop, dst, cell_index<LAT>(kp, x, y + kp.gh, z));
+    collide_store<LAT, ST, REF>(kp, pop, dst, cell_index<LAT>(kp, x, y + kp.gh, z));
 }
 
 // Two neighbouring cells' stored 16-bit values, one 32-bit word per population (low
@@ -397,14 +419,17 @@ template <int ST, int Q> struct RawPop2 {
 // smaller footprint, +2 % (FP16) / +5 % (BF16) at 4096^2.
 template <int LAT> struct MonoVals {
     float m[Lattice<LAT>::Q][Monos<2>::K];
+    int shell[Lattice<LAT>::Q];   // the velocity's shell (reference-state shift)
 };
 template <int LAT> constexpr MonoVals<LAT> make_mono_vals()
 {
     MonoVals<LAT> v{};
-    for (int i = 0; i < Lattice<LAT>::Q; ++i)
+    for (int i = 0; i < Lattice<LAT>::Q; ++i) {
         for (int k = 0; k < Monos<2>::K; ++k)
             v.m[i][k] = (float)(ipow(Lattice<LAT>::T.c[i][0], Monos<2>::M.e[k][0]) *
                                 ipow(Lattice<LAT>::T.c[i][1], Monos<2>::M.e[k][1]));
+        v.shell[i] = Lattice<LAT>::T.shell[i];
+    }
     return v;
 }
 static __constant__ MonoVals<LAT_D2Q37> c_mono_d2q37 = make_mono_vals<LAT_D2Q37>();
@@ -413,7 +438,7 @@ static __constant__ MonoVals<LAT_D2Q37> c_mono_d2q37 = make_mono_vals<LAT_D2Q37>
 // storage): the moment sums read the gathered words from registers (unrolled), the
 // relaxation, a rolled loop over opposite pairs, from their shared-memory column (word I
 // at col[I * 128]).  Per lane the arithmetic and its order are collide_store's.
-template <int LAT, int ST>
+template <int LAT, int ST, bool REF>
 __device__ __forceinline__ void collide_store_paired(const KParams<LAT> &kp, uint32_t (&rs)[Lattice<LAT>::Q],
                                                      uint32_t (&rt)[Lattice<LAT>::Q], const uint32_t *col,
                                                      typename Storage<ST>::T *__restrict__ dst, long long o)
@@ -424,12 +449,13 @@ __device__ __forceinline__ void collide_store_paired(const KParams<LAT> &kp, uin
     using V = f2;
     RawMoments<D, V> m;
     raw_moments<LAT, false>(kp, RawPop2<ST, Q>{rs, rt}, m);
+    if constexpr (REF) add_reference(kp, m);
     CellState<D, V> c;
     cell_state<LAT, true>(kp, m, c);
     EqState<D, V> e;
     es_state<LAT>(kp, c, e);
     PolyCoef<D, V, 4> pc;
-    poly_coeffs<D>(e, kp.r, kp.R2_hi, 0.f, pc);
+    poly_coeffs<false, false, false>(e, kp, pc);
     EqScalT<V> z = eq_scalars<D>(e, kp.halfNf);
     z.om1 = 1.f - kp.omega;
     z.wdrho = kp.omega * z.drho;
@@ -437,8 +463,8 @@ __device__ __forceinline__ void collide_store_paired(const KParams<LAT> &kp, uin
     z.whr = kp.omega * z.hr;
     typename Storage<ST>::T *cell = dst + o;
     const TableOff so{kp.soff};
-    relax_store<LAT, ST>(cell, so, 0, kp.omega, z, pc.k[0], Storage<ST>::cvt2(col[0]),
-                         Storage<ST>::cvt2(col[Q * 128]));
+    relax_store<LAT, ST, REF>(cell, so, 0, kp.omega, z, pc.k[0], Storage<ST>::cvt2(col[0]),
+                              Storage<ST>::cvt2(col[Q * 128]), kp.ref_wg[0], kp.ref_wh[0]);
 #pragma unroll 1
     for (int I = 1; I < Q; I += 2) {
         V E = 0.f, O = 0.f;
@@ -448,10 +474,16 @@ __device__ __forceinline__ void collide_store_paired(const KParams<LAT> &kp, uin
             if constexpr (Monos<2>::M.deg[K] % 2 == 0) E = vfma(V(mv), pc.k[K], E);
             else O = vfma(V(mv), pc.k[K], O);
         });
-        relax_store<LAT, ST>(cell, so, I, kp.omega, z, E + O, Storage<ST>::cvt2(col[I * 128]),
-                             Storage<ST>::cvt2(col[(Q + I) * 128]));
-        relax_store<LAT, ST>(cell, so, I + 1, kp.omega, z, E - O, Storage<ST>::cvt2(col[(I + 1) * 128]),
-                             Storage<ST>::cvt2(col[(Q + I + 1) * 128]));
+        float dg = 0.f, dh = 0.f;
+        if constexpr (REF) {
+            const int sh = c_mono_d2q37.shell[I];
+            dg = kp.ref_wg[sh];
+            dh = kp.ref_wh[sh];
+        }
+        relax_store<LAT, ST, REF>(cell, so, I, kp.omega, z, E + O, Storage<ST>::cvt2(col[I * 128]),
+                                  Storage<ST>::cvt2(col[(Q + I) * 128]), dg, dh);
+        relax_store<LAT, ST, REF>(cell, so, I + 1, kp.omega, z, E - O, Storage<ST>::cvt2(col[(I + 1) * 128]),
+                                  Storage<ST>::cvt2(col[(Q + I + 1) * 128]), dg, dh);
     }
 }
 
@@ -470,10 +502,10 @@ __device__ __forceinline__ uint32_t ld_pair_odd(const char *p)
 // when it is odd; the collision of both cells runs in packed FP32 pairs (one FFMA2 per
 // pair of FMAs) and both results leave in one 32-bit store.  Needs nx even.  Per cell
 // the arithmetic is the one-cell kernel's non-compensated FP32 form, evaluated per lane.
-template <int LAT, int ST, bool WALLS>
-__global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename Storage<ST>::T *__restrict__ src,
-                                                               typename Storage<ST>::T *__restrict__ dst,
-                                                               const KParams<LAT> kp, int small_y)
+template <int LAT, int ST, bool WALLS, bool REF>
+__device__ __forceinline__ void stream_collide_pair(const typename Storage<ST>::T *__restrict__ src,
+                                                    typename Storage<ST>::T *__restrict__ dst, const KParams<LAT> &kp,
+                                                    int small_y)
 {
     static_assert(Lattice<LAT>::D == 2 && ST != ST_FP32, "paired cells: 2-D lattice, 16-bit storage");
     constexpr int Q = Lattice<LAT>::Q;
@@ -550,7 +582,55 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename S
         col[I * 128] = rs[I];
         col[(Q + I) * 128] = rt[I];
     });
-    collide_store_paired<LAT, ST>(kp, rs, rt, col, dst, o);
+    collide_store_paired<LAT, ST, REF>(kp, rs, rt, col, dst, o);
+}
+
+template <int LAT, int ST, bool WALLS>
+__global__ void __launch_bounds__(128, 3) k_stream_collide_pair(const typename Storage<ST>::T *__restrict__ src,
+                                                               typename Storage<ST>::T *__restrict__ dst,
+                                                               const KParams<LAT> kp, int small_y)
+{
+    stream_collide_pair<LAT, ST, WALLS, false>(src, dst, kp, small_y);
+}
+
+// With a reference state: kp is a grid constant, so the rolled relaxation reads each
+// shell's shift at a computed constant-bank offset.
+template <int LAT, int ST, bool WALLS>
+__global__ void __launch_bounds__(128, 3) k_stream_collide_pair_ref(const typename Storage<ST>::T *__restrict__ src,
+                                                                   typename Storage<ST>::T *__restrict__ dst,
+                                                                   const __grid_constant__ KParams<LAT> kp,
+                                                                   int small_y)
+{
+    stream_collide_pair<LAT, ST, WALLS, true>(src, dst, kp, small_y);
+}
+
+// One cell's populations as deviations from rho = T = 1 (the stored values plus the
+// reference state's shift), and back.
+template <int LAT, int ST>
+__device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> &kp,
+                                          long long o, typename Storage<ST>::R *s, typename Storage<ST>::R *t)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    static_for<0, Q>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        constexpr int sh = Lattice<LAT>::T.shell[i];
+        s[i] = Storage<ST>::ld(buf + (long long)i * kp.plane + o) + kp.ref_g[sh];
+        t[i] = Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o) + kp.ref_h[sh];
+    });
+}
+
+template <int LAT, int ST>
+__device__ __forceinline__ void store_cell(typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> &kp,
+                                           long long o, const typename Storage<ST>::R *s,
+                                           const typename Storage<ST>::R *t)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    static_for<0, Q>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        constexpr int sh = Lattice<LAT>::T.shell[i];
+        Storage<ST>::st(buf + (long long)i * kp.plane + o, s[i] - kp.ref_g[sh]);
+        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, t[i] - kp.ref_h[sh]);
+    });
 }
 
 // Scaled equilibrium populations of (rho, u = r v, T) with Lambda = T delta into s[], t[].
@@ -561,9 +641,9 @@ __device__ __forceinline__ void maxwell_pops(const KParams<LAT, S> &kp, S drho, 
     constexpr int D = Lattice<LAT>::D;
     constexpr int Q = Lattice<LAT>::Q;
     EqState<D, S> e;
-    maxwell_state<D>(drho, v, kp.r, kp.R2_hi, th, e);
+    maxwell_state<D>(drho, v, kp.r, kp.r_lo, kp.R2_hi, th, e);
     PolyCoef<D, S, Lattice<LAT>::ORDER> pc;
-    poly_coeffs<D>(e, kp.r, kp.R2_hi, kp.R2_lo, pc);
+    poly_coeffs<true, true>(e, kp, pc);
     const EqScalT<S> z = eq_scalars<D>(e, kp.halfNf);
     s[0] = z.drho + pc.k[0];
     t[0] = vfma(z.hr, pc.k[0], z.hb);
@@ -642,24 +722,9 @@ __global__ void k_init(typename Storage<ST>::T *__restrict__ dst, const KParamsO
         });
     }
     const long long o = cell_index<LAT>(kp, x, ys, z);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        Storage<ST>::st(dst + (long long)i * kp.plane + o, s[i]);
-        Storage<ST>::st(dst + (long long)(Q + i) * kp.plane + o, t[i]);
-    }
+    store_cell<LAT, ST>(dst, kp, o, s, t);
 }
 
-template <int LAT, int ST>
-__device__ __forceinline__ void load_cell(const typename Storage<ST>::T *__restrict__ buf, const KParamsOf<LAT, ST> &kp,
-                                          long long o, typename Storage<ST>::R *s, typename Storage<ST>::R *t)
-{
-    constexpr int Q = Lattice<LAT>::Q;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        s[i] = Storage<ST>::ld(buf + (long long)i * kp.plane + o);
-        t[i] = Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o);
-    }
-}
 
 // Wall procedure (hybrid KBC + NEEP, Sec. VI A), one thread per (column x, wall b),
 // run on the post-collision buffer after the fluid rows were updated.  Boundary row at
@@ -696,7 +761,7 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
     RawMoments<D, R> m;
     raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s1, t1}, m);
     CellState<D, R> c;
-    cell_state<LAT>(kp, m, c);
+    cell_state<LAT, false, aux_precise<R>()>(kp, m, c);
     R ms[Q], mt[Q];
     maxwell_pops<LAT>(kp, c.drho, c.v, c.th_eq, ms, mt);
 #pragma unroll
@@ -718,6 +783,7 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
     static_for<0, Q>([&](auto II) {
         constexpr int I = decltype(II)::value;
         constexpr int cx = cv<LAT, I, 0>(), cy = cv<LAT, I, 1>(), cz = cv<LAT, I, 2>();
+        constexpr int shI = Lattice<LAT>::T.shell[I];
         if constexpr (cy != 0) {
             const int cn = cy * n;
             const R w = kp.w[I];
@@ -726,7 +792,8 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
                 const int zs = D == 3 ? wrap_sub<cz>(z, kp.nz, small_z) : 0;
                 for (int sdist = 1; sdist <= -cn; ++sdist)
                     Ld = vfma(w, Storage<ST>::ld(buf + (long long)I * kp.plane
-                                                 + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, zs)), Ld);
+                                                 + cell_index<LAT>(kp, xs, yw + n * sdist + kp.gh, zs))
+                                     + kp.ref_g[shI], Ld);
             } else {
                 W = vfma((R)cn, w, W);
                 Bd = vfma((R)cn * w, s1[I], Bd);
@@ -740,11 +807,13 @@ __device__ __forceinline__ void wall_column(typename Storage<ST>::T *__restrict_
         const long long o = cell_index<LAT>(kp, x, yw - n * k + kp.gh, z);
         // G(rho_w, u_k, T_k)/w - 1 = drw + rw * gk;   (N_f/2)(rho_w T_k G/w - 1) = drw' + rw * hk
         const R hb = kp.halfNf * drw;
+        R sk[Q], tk[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            Storage<ST>::st(buf + (long long)i * kp.plane + o, vfma(rw, gk[k][i], drw) + s1[i]);
-            Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, vfma(rw, hk[k][i], hb) + t1[i]);
+            sk[i] = vfma(rw, gk[k][i], drw) + s1[i];
+            tk[i] = vfma(rw, hk[k][i], hb) + t1[i];
         }
+        store_cell<LAT, ST>(buf, kp, o, sk, tk);
     }
 }
 
@@ -773,7 +842,7 @@ __global__ void k_moments(const typename Storage<ST>::T *__restrict__ buf, const
     RawMoments<D, R> m;
     raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s, t}, m);
     CellState<D, R> c;
-    cell_state<LAT>(kp, m, c);
+    cell_state<LAT, false, aux_precise<R>()>(kp, m, c);
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
     if (rho) rho[f] = 1.0 + (double)c.drho;
@@ -863,7 +932,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const typename Storage<ST
         RawMoments<D, R> m;
         raw_moments<LAT, aux_precise<R>()>(kp, ArrayPopT<R>{s, t}, m);
         CellState<D, R> c;
-        cell_state<LAT>(kp, m, c);
+        cell_state<LAT, false, aux_precise<R>()>(kp, m, c);
         acc[0] += (double)m.drho;
         for (int a = 0; a < D; ++a) acc[1 + a] += (double)kp.r * (double)m.J[a];
         R trM = 0.f;
@@ -902,11 +971,16 @@ __global__ void k_get_pops(const typename Storage<ST>::T *__restrict__ buf, cons
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    for (int i = 0; i < Q; ++i) {
+    static_for<0, Q>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        constexpr int sh = Lattice<LAT>::T.shell[i];
         const double w = kp.w[i];
-        if (g) g[i * n + f] = w * (1.0 + (double)Storage<ST>::ld(buf + (long long)i * kp.plane + o));
-        if (h) h[i * n + f] = w * ((double)kp.halfNf + (double)Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o));
-    }
+        // the reference shift added in FP64
+        if (g) g[i * n + f] = w * (1.0 + (double)kp.ref_g[sh] + (double)Storage<ST>::ld(buf + (long long)i * kp.plane + o));
+        if (h)
+            h[i * n + f] = w * ((double)kp.halfNf + (double)kp.ref_h[sh]
+                                + (double)Storage<ST>::ld(buf + (long long)(Q + i) * kp.plane + o));
+    });
 }
 
 template <int LAT, int ST>
@@ -920,12 +994,16 @@ __global__ void k_set_pops(typename Storage<ST>::T *__restrict__ buf, const KPar
     const long long n = (long long)kp.nx * kp.ny * kp.nz;
     const long long f = ((long long)z * kp.ny + y) * kp.nx + x;
     const long long o = cell_index<LAT>(kp, x, y + kp.gh, z);
-    for (int i = 0; i < Q; ++i) {
+    using R = typename Storage<ST>::R;
+    static_for<0, Q>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        constexpr int sh = Lattice<LAT>::T.shell[i];
         const double w = kp.w[i];
-        using R = typename Storage<ST>::R;
-        Storage<ST>::st(buf + (long long)i * kp.plane + o, (R)(g[i * n + f] / w - 1.0));
-        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o, (R)(h[i * n + f] / w - (double)kp.halfNf));
-    }
+        // the reference shift subtracted in FP64, before the rounding to the storage form
+        Storage<ST>::st(buf + (long long)i * kp.plane + o, (R)(g[i * n + f] / w - 1.0 - (double)kp.ref_g[sh]));
+        Storage<ST>::st(buf + (long long)(Q + i) * kp.plane + o,
+                        (R)(h[i * n + f] / w - (double)kp.halfNf - (double)kp.ref_h[sh]));
+    });
 }
 
 } // namespace lbm

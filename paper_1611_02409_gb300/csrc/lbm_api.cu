@@ -167,6 +167,8 @@ static int map_params(const lbm_params &p, Mapped &m)
         return set_err(nullptr, LBM_ERR_ARG, "kappa = 1 leaves no freedom for Pr != 1");
     if (p.bc_y == LBM_WALLS && !(p.wall_T[0] > 0 && p.wall_T[1] > 0))
         return set_err(nullptr, LBM_ERR_ARG, "wall temperatures must be > 0");
+    if (!(p.rho0 == 0 || (p.rho0 > 0 && std::isfinite(p.rho0))) || !(p.T0 == 0 || (p.T0 > 0 && std::isfinite(p.T0))))
+        return set_err(nullptr, LBM_ERR_ARG, "reference state: rho0 and T0 must be > 0 (or 0 for 1)");
     if (p.pr_mode == LBM_PR_LITERAL) {
         m.omega = p.Pr / p.tau;             // rate Pr/tau_f (Eq. DiscreteReductionG)
         m.tau_s = p.tau;
@@ -221,6 +223,8 @@ int make_ctx(const lbm_params &pin, Ctx &c, int *D_out, int *Q_out, double *r_ou
         for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
         c.wall_T[b] = p.wall_T[b];
     }
+    c.rho0 = p.rho0 == 0 ? 1.0 : p.rho0;
+    c.T0 = p.T0 == 0 ? 1.0 : p.T0;
     c.kernel = 1;
     if (D_out) *D_out = mp.D;
     if (Q_out) *Q_out = Q;
@@ -318,6 +322,8 @@ int lbm_create(const lbm_params *pin, void *stream, lbm_handle **out)
         for (int d = 0; d < 3; ++d) c.wall_u[b][d] = p.wall_u[b][d];
         c.wall_T[b] = p.wall_T[b];
     }
+    c.rho0 = p.rho0 == 0 ? 1.0 : p.rho0;
+    c.T0 = p.T0 == 0 ? 1.0 : p.T0;
     h->ops = lbm::ops_for(p.lattice, p.storage);
     h->elem = (size_t)lbm::storage_bytes(p.storage);
     h->buf_elems = (size_t)2 * h->Q * (size_t)c.plane;

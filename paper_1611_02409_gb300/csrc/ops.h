@@ -15,6 +15,7 @@ struct Ctx {
     int open_x;            // open (zero-gradient) x ends
     int num_sms;
     int kernel;            // LBM_KERNEL_*: 1 direct, 2 staged, 3 paired, 4 two-pass
+    double rho0, T0;       // reference state of the stored deviations
 };
 
 // Bytes of one stored population in storage form LBM_FP32 (0), LBM_FP16 (1), LBM_BF16 (2)

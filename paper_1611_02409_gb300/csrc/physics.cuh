@@ -3,7 +3,10 @@
 // Storage convention (all precisions): s_i = (g_i - w_i)/w_i and t_i = (h_i - w_i N_f/2)/w_i,
 // i.e. deviations from the rest state rho = T = 1 (u = 0) scaled by the weight, so the
 // small departures that carry the flow keep their full relative precision in FP32 and
-// stay in the normal range of FP16/BF16.
+// stay in the normal range of FP16/BF16.  A handle with a reference state (rho0, T0)
+// stores them less that state's rest equilibrium (KParams::ref_*): the arithmetic below
+// still works with deviations from rho = T = 1, the moment sums take the reference's
+// constant share and the relaxation's target is shifted by it.
 //
 // Moments (Sec. V): rho = sum g_i, rho u = sum g_i xi_i, the second moment
 // sum g_i xi_i xi_i, rho e_int = sum h_i; temperatures T_tr, T_int, T_eq, T_rel and the
@@ -134,6 +137,22 @@ template <int LAT, class S = float> struct KParams {
     // population p (p < Q: g_p, else h_{p-Q}) for a cell away from the periodic seams,
     // and of its destination; the gather then needs no per-population index arithmetic.
     long long goff[2 * Q], soff[2 * Q];
+    // Reference state (rho0, T0) of the stored deviations: s_i = g_i/w_i - 1 - dg_i and
+    // t_i = h_i/w_i - N_f/2 - dh_i, with dg_i = rho0 phi_i - 1, dh_i = (N_f/2)(rho0 T0 phi_i - 1)
+    // and phi_i the rest equilibrium at T0 relative to the weight (a function of |c_i| only,
+    // so one value per shell).  All zero for rho0 = T0 = 1.  ref_wg, ref_wh: omega dg, omega dh
+    // (16-bit relaxation).  ref_hi + ref_lo: the reference's share of the raw moments,
+    // sum_i w_i dg_i (drho), sum_i w_i dh_i (H) and sum_i w_i dg_i c_ia^2 (M_aa, a = 0..2),
+    // from the rounded dg, dh, so that the collision conserves exactly what it sums.
+    S ref_g[Lattice<LAT>::NSHELL], ref_h[Lattice<LAT>::NSHELL];
+    S ref_wg[Lattice<LAT>::NSHELL], ref_wh[Lattice<LAT>::NSHELL];
+    S ref_hi[5], ref_lo[5];
+    // r - (S)r, and r^m / alpha! (m = |alpha| = 3, 4) as hi + lo for each monomial alpha of
+    // the fourth-order polynomial: with them the lattice sums of the equilibrium close on
+    // the exact constants (a rounded r^4 / 4! shifts the equilibrium's mass by that
+    // rounding times its O((T - 1)^2) fourth-order part, the same in every cell and step).
+    S r_lo;
+    S cm_hi[Monos<Lattice<LAT>::D>::K], cm_lo[Monos<Lattice<LAT>::D>::K];
 };
 
 // State that the equilibrium needs, in deviation form.  The leading (first-order) parts
@@ -260,9 +279,17 @@ __device__ __forceinline__ void burnett_terms(const EqState<2, V> &s, float r, P
 // Coefficients of rho q(xi) in the monomials of c (xi = r c): K_alpha = rho r^|alpha| C_alpha / alpha!
 // for the fourth-order expansion (Eq. GExpansion); with N = 6 (2-D) the fifth- and
 // sixth-order terms are added.
-template <int D, class V, int N, class S>
-__device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, S r, S R2_hi, S R2_lo, PolyCoef<D, V, N> &pc)
+// PRECISE: r^2 as hi + lo (FP32 storage).  EXACT (with PRECISE): the third- and
+// fourth-order constants r^m / alpha! as hi + lo too; their rounding shifts the
+// equilibrium's mass, momentum and energy in proportion to its (T - 1) terms, negligible
+// near the lattice's unit temperature and compiled in for handles with a reference state.
+// Otherwise CM: the constants r^m / alpha! from the launch parameters (one product per
+// coefficient), else r^m and 1/alpha! formed in the kernel.
+template <bool PRECISE, bool EXACT, bool CM = true, int D, class V, int N, class KP>
+__device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, const KP &kp, PolyCoef<D, V, N> &pc)
 {
+    using S = typename ScalarOf<V>::type;
+    const S r = kp.r, R2_hi = kp.R2_hi, R2_lo = PRECISE ? kp.R2_lo : S(0);
     const auto &A = s.A;
     const auto &u = s.u;
     const V rho = s.rho;
@@ -324,8 +351,14 @@ __device__ __forceinline__ void poly_coeffs(const EqState<D, V> &s, S r, S R2_hi
         else if constexpr (m == 1) v = k1[i0];
         else if constexpr (m == 2) {
             // r^2 in hi + lo so that the mass and energy sums close on the same constant
+            // (inv = 1 or 1/2, exact)
             const V x = inv * c2[i0][i1];
             v = vfma(R2_hi, x, R2_lo * x);
+        } else if constexpr (PRECISE && EXACT) {
+            const V y = rho * (m == 3 ? c3_of<D, V>(A, u, i0, i1, i2) : c4_of<D, V>(A, u, i0, i1, i2, i3));
+            v = vfma(kp.cm_hi[K], y, kp.cm_lo[K] * y);
+        } else if constexpr (!PRECISE && CM) {
+            v = kp.cm_hi[K] * (rho * (m == 3 ? c3_of<D, V>(A, u, i0, i1, i2) : c4_of<D, V>(A, u, i0, i1, i2, i3)));
         }
         else if constexpr (m == 3) v = r3 * inv * rho * c3_of<D, V>(A, u, i0, i1, i2);
         else v = r4 * inv * rho * c4_of<D, V>(A, u, i0, i1, i2, i3);
@@ -371,6 +404,18 @@ template <int D, class V = float> struct RawMoments {
     V M[D][D];            // sum g~ c c
     V H;                  // sum h~
 };
+
+// The reference state's share of the raw moments (see KParams::ref_*), added as hi + lo
+// so that no constant rounding error enters the conserved sums.
+template <int LAT, class S, class V>
+__device__ __forceinline__ void add_reference(const KParams<LAT, S> &kp, RawMoments<Lattice<LAT>::D, V> &m)
+{
+    constexpr int D = Lattice<LAT>::D;
+    m.drho = (m.drho + V(kp.ref_lo[0])) + V(kp.ref_hi[0]);
+    m.H = (m.H + V(kp.ref_lo[1])) + V(kp.ref_hi[1]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) m.M[a][a] = (m.M[a][a] + V(kp.ref_lo[2 + a])) + V(kp.ref_hi[2 + a]);
+}
 
 // Population accessors: pop.template sv<I>() / tv<I>() return the scaled deviations s_I,
 // t_I of one cell (from registers, or from a shared-memory tile) as V; refresh() is
@@ -516,7 +561,10 @@ template <class V> __device__ __forceinline__ V fast_inv(V x);
 template <> __device__ __forceinline__ float fast_inv<float>(float x) { return __fdividef(1.f, x); }
 template <> __device__ __forceinline__ f2 fast_inv<f2>(f2 x) { return f2(__fdividef(1.f, x.x), __fdividef(1.f, x.y)); }
 
-template <int LAT, bool FASTDIV = false, class V, class S>
+// PRECISE: u = r v with r as hi + lo (a rounded r scales the velocity of the equilibrium's
+// third- and fourth-order terms by the same factor in every cell, a momentum bias in
+// proportion to T - 1: used with the exact constants of poly_coeffs).
+template <int LAT, bool FASTDIV = false, bool PRECISE = false, class V, class S>
 __device__ __forceinline__ void cell_state(const KParams<LAT, S> &kp, const RawMoments<Lattice<LAT>::D, V> &m,
                                            CellState<Lattice<LAT>::D, V> &c)
 {
@@ -529,7 +577,8 @@ __device__ __forceinline__ void cell_state(const KParams<LAT, S> &kp, const RawM
     for (int a = 0; a < D; ++a) {
         c.J[a] = m.J[a];
         c.v[a] = m.J[a] * c.inv_rho;
-        c.u[a] = kp.r * c.v[a];
+        if constexpr (PRECISE) c.u[a] = vfma(V(kp.r), c.v[a], V(kp.r_lo) * c.v[a]);
+        else c.u[a] = kp.r * c.v[a];
     }
     V tr = 0.f;
 #pragma unroll
@@ -594,7 +643,7 @@ __device__ __forceinline__ void es_state(const KParams<LAT, S> &kp, const CellSt
 
 // Maxwellian state (Lambda = T delta) of (rho, u = r v, T) given the lattice velocity v.
 template <int D, class R>
-__device__ __forceinline__ void maxwell_state(R drho, const R (&v)[D], R r, R R2_hi, R th, EqState<D, R> &e)
+__device__ __forceinline__ void maxwell_state(R drho, const R (&v)[D], R r, R r_lo, R R2_hi, R th, EqState<D, R> &e)
 {
     e.drho = drho;
     e.rho = 1.f + drho;
@@ -604,7 +653,7 @@ __device__ __forceinline__ void maxwell_state(R drho, const R (&v)[D], R r, R R2
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         e.J[a] = e.rho * v[a];
-        e.u[a] = r * v[a];
+        e.u[a] = vfma(r, v[a], r_lo * v[a]);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a)

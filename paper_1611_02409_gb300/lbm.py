@@ -62,17 +62,19 @@ class lbm_params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("Pr", C.c_double), ("gamma", C.c_double), ("N_f", C.c_double),
                 ("kappa", C.c_double), ("tau", C.c_double), ("pr_mode", C.c_int), ("storage", C.c_int),
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc_y", C.c_int),
-                ("wall_u", (C.c_double * 3) * 2), ("wall_T", C.c_double * 2), ("bc_x", C.c_int)]
+                ("wall_u", (C.c_double * 3) * 2), ("wall_T", C.c_double * 2), ("bc_x", C.c_int),
+                ("rho0", C.c_double), ("T0", C.c_double)]
 
 
 def make_params(lattice=LBM_D2Q37, Pr=0.71, gamma=1.4, N_f=0.0, kappa=0.2, tau=0.6, pr_mode=LBM_PR_SHIFTED,
                 storage=LBM_FP32, nx=64, ny=64, nz=1, bc_y=LBM_PERIODIC, wall_u=None, wall_T=None,
-                bc_x=LBM_PERIODIC) -> lbm_params:
+                bc_x=LBM_PERIODIC, rho0=1.0, T0=1.0) -> lbm_params:
     p = lbm_params()
     p.lattice, p.Pr, p.gamma, p.N_f, p.kappa, p.tau = lattice, Pr, gamma, N_f, kappa, tau
     p.pr_mode = pr_mode
     p.storage = STORAGE.get(storage, storage) if isinstance(storage, str) else storage
     p.nx, p.ny, p.nz, p.bc_y, p.bc_x = nx, ny, nz, bc_y, bc_x
+    p.rho0, p.T0 = rho0, T0
     wu = np.zeros((2, 3)) if wall_u is None else np.asarray(wall_u, float).reshape(2, 3)
     wT = np.ones(2) if wall_T is None else np.asarray(wall_T, float).reshape(2)
     for b in range(2):

@@ -58,6 +58,15 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
     assert m["warn"] == (m["nuG"] < -0.5)
 
 
+def test_reference_state_fields_default_and_zero(L):
+    # lbm_params ends with the reference state; 0 reads as 1 and the mapping ignores it
+    assert [f[0] for f in L.lbm_params._fields_][-2:] == ["rho0", "T0"]
+    assert L.make_params().rho0 == 1.0 and L.make_params().T0 == 1.0
+    base = L.lbm_map_params(L.make_params())
+    for ref in (dict(rho0=0.0, T0=0.0), dict(rho0=1.3, T0=0.8)):
+        assert L.lbm_map_params(L.make_params(**ref)) == base
+
+
 @pytest.mark.parametrize("bad", [dict(lattice=7), dict(tau=0.5), dict(Pr=0.0), dict(kappa=0.0), dict(kappa=1.2),
                                  dict(gamma=2.5), dict(gamma=1.0), dict(nx=0), dict(bc_y=1, ny=4),
                                  dict(storage=9), dict(pr_mode=4),
@@ -66,7 +75,8 @@ def test_parameter_mapping_matches_oracle(L, Pr, gamma, kappa, tau, mode):
                                  dict(lattice=4, bc_y=1, ny=16),
                                  dict(bc_x=5), dict(lattice=2, bc_x=2),
                                  dict(nx=4, ny=65536), dict(nx=4, ny=65532, bc_y=1),
-                                 dict(lattice=2, nx=4, ny=4, nz=65536)])
+                                 dict(lattice=2, nx=4, ny=4, nz=65536),
+                                 dict(rho0=-1.0), dict(T0=-0.5), dict(T0=float("nan")), dict(rho0=float("inf"))])
 def test_invalid_parameters_rejected_without_gpu(L, bad):
     p = L.make_params(**bad)
     with pytest.raises(L.LbmError) as e:
