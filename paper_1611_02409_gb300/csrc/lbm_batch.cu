@@ -37,9 +37,11 @@ struct Inst {
 };
 
 // One chunk of `CPT` x 128 consecutive fluid cells (row-major over the computed rows) of
-// one instance per work item; the instance's launch parameters are staged in shared
-// memory whenever the work item's instance changes.
-template <int CPT>
+// one instance per work item; each block takes a contiguous range of work items, so
+// consecutive items mostly belong to one instance, whose launch parameters are staged in
+// shared memory whenever the item's instance changes.  REF: some instance of the batch has
+// a reference state (the step with the reference's shifts, zero for the others).
+template <int CPT, bool REF>
 __global__ void __launch_bounds__(kThreads, 4) k_bstep(const Inst *__restrict__ inst, const KP *__restrict__ kps,
                                                        const int2 *__restrict__ work, const int *__restrict__ nwork,
                                                        float *__restrict__ arena)
@@ -47,8 +49,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bstep(const Inst *__restrict__ 
     __shared__ __align__(16) long long skp_raw[(sizeof(KP) + 7) / 8];
     const KP &kp = *reinterpret_cast<const KP *>(skp_raw);
     const int nw = nwork[0];
+    const int per = (nw + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int w0 = blockIdx.x * per, w1 = min(nw, w0 + per);
     int cached = -1;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    for (int w = w0; w < w1; ++w) {
         const int2 it = work[w];
         if (it.x != cached) {
             __syncthreads();
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bstep(const Inst *__restrict__ 
                 t[I] = __ldg(src + ((Q + I) * pl + idx));
             });
             const int o = (y + gh) * nx + x;
-            collide_store<LAT, ST>(kp, ArrayPop{s, t}, dst, o, StrideOff<4>{pl});
+            collide_store<LAT, ST, REF>(kp, ArrayPop{s, t}, dst, o, StrideOff<4>{pl});
         }
     }
 }
@@ -235,6 +239,7 @@ struct lbm_batch {
     int g_tile = 0, g_window = 0;
     double g_tol = 0.0;
     int tile = 128;                 // cells per work item
+    bool ref = false;               // some instance has a reference state
     int num_sms = 0;
     std::string err;
 };
@@ -253,12 +258,18 @@ int bfail(lbm_batch *b, int code, const std::string &m)
         if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-int step_grid(int tile, int num_sms)
+using StepFn = void (*)(const Inst *, const KP *, const int2 *, const int *, float *);
+
+StepFn step_kernel(int tile, bool ref)
+{
+    if (ref) return tile == 512 ? k_bstep<4, true> : tile == 256 ? k_bstep<2, true> : k_bstep<1, true>;
+    return tile == 512 ? k_bstep<4, false> : tile == 256 ? k_bstep<2, false> : k_bstep<1, false>;
+}
+
+int step_grid(int tile, bool ref, int num_sms)
 {
     int nb = 0;
-    if (tile == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bstep<4>, kThreads, 0);
-    else if (tile == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bstep<2>, kThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bstep<1>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel(tile, ref), kThreads, 0);
     return (nb > 0 ? nb : 1) * num_sms;
 }
 
@@ -269,13 +280,12 @@ void launch_window(lbm_batch *b, int window, double tol, int tile)
     // of all instances (the work list only shrinks as instances converge)
     long long items = 0;
     for (const Inst &in : b->inst0) items += (in.ncomp + tile - 1) / tile;
-    const int grid = (int)std::max(1LL, std::min((long long)step_grid(tile, b->num_sms), items));
+    const int grid = (int)std::max(1LL, std::min((long long)step_grid(tile, b->ref, b->num_sms), items));
+    const StepFn kstep = step_kernel(tile, b->ref);
     k_bwork_offsets<<<1, 32, 0, b->stream>>>(b->d_inst, n, tile, b->d_off, b->d_nwork);
     k_bwork_fill<<<n, 128, 0, b->stream>>>(b->d_inst, tile, b->d_off, b->d_work);
     for (int s = 0; s < window; ++s) {
-        if (tile == 512) k_bstep<4><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
-        else if (tile == 256) k_bstep<2><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
-        else k_bstep<1><<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
+        kstep<<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
         k_bwalls_flip<<<n, 64, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena);
     }
     k_bresid<<<n, 256, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena, window, tol);
@@ -347,6 +357,7 @@ int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out)
             return set_global_error(LBM_ERR_ARG, "a batched instance's 2 Q planes must hold fewer than 2^31 values");
         }
         kps[i] = make_kparams<LAT>(c);
+        b->ref = b->ref || has_reference(c);
         Inst &in = b->inst0[i];
         memset(&in, 0, sizeof(in));
         const size_t pop = (size_t)2 * Q * c.plane;
