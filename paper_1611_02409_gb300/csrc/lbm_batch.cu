@@ -120,20 +120,29 @@ __global__ void k_bwalls_flip(Inst *__restrict__ inst, const KP *__restrict__ kp
     }
 }
 
-// Residual max_{X in u_x, T} ||X - X_prev|| / (m ||X||) of every active instance (one
-// block each, FP64 sums); below `tol` the instance becomes inactive.
-__global__ void __launch_bounds__(256) k_bresid(Inst *inst, const KP *__restrict__ kps, float *arena, int m,
-                                                double tol)
+// Residual max_{X in u_x, T} ||X - X_prev|| / (m ||X||) of every active instance, FP64
+// sums in a fixed order (deterministic).  Stage 1: block (i, k) sums chunk k (kResChunk
+// cells) of instance i into partials[i][k] and refreshes the snapshot of its cells;
+// stage 2: one thread per instance adds its chunks' partials in order and decides;
+// below `tol` the instance becomes inactive.
+constexpr int kResThreads = 256;
+constexpr int kResChunk = 16 * kResThreads;
+
+__global__ void __launch_bounds__(kResThreads) k_bresid_part(const Inst *__restrict__ inst, const KP *__restrict__ kps,
+                                                             float *arena, int maxchunks, double *partials)
 {
-    Inst &d = inst[blockIdx.x];
+    const Inst &d = inst[blockIdx.x];
     if (!d.active) return;
     const KP &kp = kps[blockIdx.x];
+    const int n = kp.nx * kp.ny;
+    const int f0 = blockIdx.y * kResChunk;
+    if (f0 >= n) return;
+    const int f1 = min(n, f0 + kResChunk);
     const float *buf = arena + d.buf[d.cur];
     float *snap = arena + d.snap;
-    const int n = kp.nx * kp.ny;
     const int have = d.have_snap;
     double a[4] = {0, 0, 0, 0};
-    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+    for (int f = f0 + threadIdx.x; f < f1; f += kResThreads) {
         const int x = f % kp.nx, y = f / kp.nx;
         float s[Q], t[Q];
         load_cell<LAT, ST>(buf, kp, (long long)(y + kp.gh) * kp.nx + x, s, t);
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(256) k_bresid(Inst *inst, const KP *__restrict
         snap[f] = ux;
         snap[n + f] = th;
     }
-    __shared__ double sh[8][4];
+    __shared__ double sh[kResThreads / 32][4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -160,25 +169,39 @@ __global__ void __launch_bounds__(256) k_bresid(Inst *inst, const KP *__restrict
         if (lane == 0) sh[wid][v] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[4] = {0, 0, 0, 0};
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
-            for (int v = 0; v < 4; ++v) t[v] += sh[w][v];
-        // a non-finite field makes its sums NaN (the comparisons below would read those as
-        // zero): report NaN and stop the instance
-        const bool bad = isnan(t[0]) || isnan(t[1]) || isnan(t[2]) || isnan(t[3]);
-        if (bad) {
-            d.residual = NAN;
-            d.active = 0;
-        } else if (have) {
-            const double ru = t[1] > 0 ? sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
-            const double rT = t[3] > 0 ? sqrt(t[2] / t[3]) : 0.0;
-            d.residual = fmax(ru, rT) / m;
-            if (d.residual < tol) d.active = 0;  // converged
-        } else {
-            d.residual = INFINITY;
-            d.have_snap = 1;
-        }
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < kResThreads / 32; ++w) t += sh[w][threadIdx.x];
+        partials[((long long)blockIdx.x * maxchunks + blockIdx.y) * 4 + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_bresid_final(Inst *inst, const KP *__restrict__ kps, int n_inst, int maxchunks,
+                               const double *__restrict__ partials, int m, double tol)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    Inst &d = inst[i];
+    if (!d.active) return;
+    const int n = kps[i].nx * kps[i].ny;
+    const int nch = (n + kResChunk - 1) / kResChunk;
+    double t[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nch; ++k)
+        for (int v = 0; v < 4; ++v) t[v] += partials[((long long)i * maxchunks + k) * 4 + v];
+    // a non-finite field makes its sums NaN (the comparisons below would read those as
+    // zero): report NaN and stop the instance
+    const bool bad = isnan(t[0]) || isnan(t[1]) || isnan(t[2]) || isnan(t[3]);
+    if (bad) {
+        d.residual = NAN;
+        d.active = 0;
+    } else if (d.have_snap) {
+        const double ru = t[1] > 0 ? sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
+        const double rT = t[3] > 0 ? sqrt(t[2] / t[3]) : 0.0;
+        d.residual = fmax(ru, rT) / m;
+        if (d.residual < tol) d.active = 0;  // converged
+    } else {
+        d.residual = INFINITY;
+        d.have_snap = 1;
     }
 }
 
@@ -232,6 +255,8 @@ struct lbm_batch {
     size_t arena_elems = 0;
     int2 *d_work = nullptr;
     int *d_off = nullptr;
+    double *d_rpart = nullptr;      // residual partial sums [instance][chunk][4]
+    int maxchunks = 1;
     int *d_nwork = nullptr;
     int *h_nwork = nullptr;         // pinned
     cudaStream_t stream = nullptr;
@@ -288,7 +313,10 @@ void launch_window(lbm_batch *b, int window, double tol, int tile)
         kstep<<<grid, kThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_work, b->d_nwork, b->d_arena);
         k_bwalls_flip<<<n, 64, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena);
     }
-    k_bresid<<<n, 256, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena, window, tol);
+    k_bresid_part<<<dim3(n, b->maxchunks), kResThreads, 0, b->stream>>>(b->d_inst, b->d_kp, b->d_arena,
+                                                                         b->maxchunks, b->d_rpart);
+    k_bresid_final<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_inst, b->d_kp, n, b->maxchunks, b->d_rpart, window,
+                                                           tol);
     k_bcount<<<1, 32, 0, b->stream>>>(b->d_inst, n, b->d_nwork);
 }
 
@@ -376,6 +404,7 @@ int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out)
             in.wp.thw[bb] = (float)(c.wall_T[bb] - 1.0);
         }
         max_items += (in.ncomp + kThreads - 1) / kThreads;
+        b->maxchunks = std::max(b->maxchunks, (c.nx * c.ny + kResChunk - 1) / kResChunk);
     }
     b->arena_elems = off;
     int dev = 0;
@@ -387,6 +416,7 @@ int lbm_batch_create(int n, const lbm_params *params, lbm_batch **out)
     if (e == cudaSuccess) e = cudaMalloc(&b->d_kp, sizeof(KP) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(int2) * (max_items + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_off, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rpart, sizeof(double) * 4 * n * (size_t)b->maxchunks);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_nwork, sizeof(int) * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_nwork, sizeof(int) * 2);
     if (e == cudaSuccess)
@@ -415,6 +445,7 @@ int lbm_batch_destroy(lbm_batch *b)
     cudaFree(b->d_kp);
     cudaFree(b->d_work);
     cudaFree(b->d_off);
+    cudaFree(b->d_rpart);
     cudaFree(b->d_nwork);
     if (b->h_nwork) cudaFreeHost(b->h_nwork);
     if (b->stream) cudaStreamDestroy(b->stream);
