@@ -86,6 +86,29 @@ def test_batch_instances_converge_independently(L):
     bt.close()
 
 
+def test_batch_residual_spans_several_chunks(L):
+    # the residual is summed in chunks of 4096 cells: instances of 1, 3 (ragged) and 10
+    # chunks against the definition evaluated on the reported fields
+    cases = [dict(nx=40, ny=40, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.6),
+             dict(nx=96, ny=96, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.6),
+             dict(nx=256, ny=160, Pr=0.71, gamma=1.4, kappa=0.2, tau=0.6)]
+    bt = L.Batch(cases)
+    for i, c in enumerate(cases):
+        bt.init(i, *inputs.taylor_green_2d(c["nx"], ny=c["ny"], U0=0.02, T_amp=0.01))
+    bt.run(100, tol=0.0, check_every=100)
+    m1 = [bt.moments(i) for i in range(len(cases))]
+    bt.run(100, tol=0.0, check_every=100)     # tol 0 keeps every instance active
+    steps, res, act = bt.status()
+    assert list(steps) == [200] * 3
+    for i in range(len(cases)):
+        m2 = bt.moments(i)
+        ru = np.linalg.norm(m2["u"][0] - m1[i]["u"][0]) / np.linalg.norm(m2["u"][0])
+        rT = np.linalg.norm(m2["T"] - m1[i]["T"]) / np.linalg.norm(m2["T"])
+        want = max(ru, rT) / 100
+        assert res[i] == pytest.approx(want, rel=1e-4), (i, res[i], want)
+    bt.close()
+
+
 def test_batch_autotune(L):
     bt = L.Batch(CASES)
     tile = bt.autotune(10)
