@@ -243,6 +243,14 @@ int lbm_debug_inject_stall(lbm_handle *h, int on);
  * count (0: every access in bounds), or minus an LBM status for invalid parameters or a
  * variant the configuration does not admit. */
 long long lbm_debug_index_audit(const lbm_params *p, int variant, int wrap_threshold);
+/* The reference state's shifts as the kernels use them (tests only; no device work): for
+ * the configuration *p (its rho0, T0), dg[i] and dh[i] receive the shift of velocity i's
+ * stored g and h deviations (host arrays of Q doubles, the library's velocity order; the
+ * rest equilibrium at (rho0, T0) over the weight, less rho = T = 1, Sec. IV), and
+ * share[0..4] the reference's share of the moment sums sum_i w_i dg_i, sum_i w_i dh_i and
+ * sum_i w_i dg_i c_ia^2 (a = x, y, z; each as its hi + lo pair summed).  Returns Q, or
+ * minus an LBM status for invalid parameters. */
+int lbm_debug_reference_state(const lbm_params *p, double *dg, double *dh, double *share);
 /* variant value for lbm_debug_index_audit: the batched step's addressing for one instance
  * (D2Q37, FP32, periodic x; also checks that its 32-bit offsets do not overflow) */
 #define LBM_AUDIT_BATCH 5

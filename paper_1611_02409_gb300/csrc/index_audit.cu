@@ -369,3 +369,39 @@ extern "C" long long lbm_debug_index_audit(const lbm_params *p, int variant, int
     default: return -LBM_ERR_ARG;
     }
 }
+
+// The shifts exactly as make_kparams hands them to the kernels (FP32 launch parameters,
+// widened).
+namespace {
+template <int LAT> int reference_state(const lbm::Ctx &c, double *dg, double *dh, double *share)
+{
+    using namespace lbm;
+    const KParams<LAT> kp = make_kparams<LAT>(c);
+    for (int i = 0; i < Lattice<LAT>::Q; ++i) {
+        const int sh = Lattice<LAT>::T.shell[i];
+        if (dg) dg[i] = kp.ref_g[sh];
+        if (dh) dh[i] = kp.ref_h[sh];
+    }
+    if (share)
+        for (int k = 0; k < 5; ++k) share[k] = (double)kp.ref_hi[k] + (double)kp.ref_lo[k];
+    return Lattice<LAT>::Q;
+}
+} // namespace
+
+extern "C" int lbm_debug_reference_state(const lbm_params *p, double *dg, double *dh, double *share)
+{
+    using namespace lbm;
+    if (!p) return -LBM_ERR_ARG;
+    Ctx c;
+    int D = 0, Q = 0;
+    double r = 0.0;
+    const int rc = make_ctx(*p, c, &D, &Q, &r);
+    if (rc != LBM_OK && rc != LBM_WARN_PR_RANGE) return -rc;
+    switch (p->lattice) {
+    case LBM_D2Q37: return reference_state<LAT_D2Q37>(c, dg, dh, share);
+    case LBM_D3Q103: return reference_state<LAT_D3Q103>(c, dg, dh, share);
+    case LBM_D2Q33: return reference_state<LAT_D2Q33>(c, dg, dh, share);
+    case LBM_D2Q77: return reference_state<LAT_D2Q77>(c, dg, dh, share);
+    default: return -LBM_ERR_ARG;
+    }
+}

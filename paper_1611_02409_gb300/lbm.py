@@ -111,6 +111,7 @@ def lib():
             L.lbm_lattice_unit_scale.argtypes = [C.c_int, dp]
             L.lbm_debug_index_audit.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_int]
             L.lbm_debug_index_audit.restype = C.c_longlong
+            L.lbm_debug_reference_state.argtypes = [C.POINTER(lbm_params), dp, dp, dp]
             L.lbm_map_params.argtypes = [C.POINTER(lbm_params), dp]
             L.lbm_coefficients.argtypes = [vp, dp]
             L.lbm_init_fields.argtypes = [vp, vp, vp, vp, C.c_int]
@@ -182,6 +183,18 @@ def lbm_debug_index_audit(p: lbm_params, variant: int, wrap_threshold: int = 0) 
     if n < 0:
         raise LbmError(int(-n), "index audit: invalid configuration or variant")
     return n
+
+
+def lbm_debug_reference_state(p: lbm_params):
+    """The reference state's per-velocity shifts dg, dh and moment shares as the kernels
+    use them (host only); raises on invalid parameters."""
+    Q = len(lbm_lattice_table(p.lattice)[2])
+    dg, dh, share = np.zeros(Q), np.zeros(Q), np.zeros(5)
+    f = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    q = lib().lbm_debug_reference_state(C.byref(p), f(dg), f(dh), f(share))
+    if q < 0:
+        raise LbmError(int(-q), "reference state: invalid configuration")
+    return dg, dh, share
 
 
 def lbm_map_params(p: lbm_params) -> dict:
