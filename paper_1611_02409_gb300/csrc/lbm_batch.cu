@@ -26,11 +26,11 @@ constexpr int ST = ST_FP32;
 constexpr int Q = Lattice<LAT>::Q;
 using KP = KParams<LAT>;
 constexpr int kThreads = 128;
-// Work items a block takes in a row before moving on by the grid's stride: consecutive
-// items mostly share an instance (its parameters stay staged), while the resident blocks
-// together sweep one band of the work list at a time (DRAM locality).  Measured with 128-
-// cell items: 16 against 2, 4, 8, 32 and one contiguous range per block (a 4096^2
-// instance 9.07 GLUPS against 8.63 contiguous; 64 x 512^2 and 256 uneven squares
+// Work items a block takes in a row (at most) before moving on by the grid's stride:
+// consecutive items mostly share an instance (its parameters stay staged), while the
+// resident blocks together sweep one band of the work list at a time (DRAM locality).
+// Measured with 128-cell items: 16 against 2, 4, 8, 32 and one contiguous range per block
+// (a 4096^2 instance 9.07 GLUPS against 8.63 contiguous; 64 x 512^2 and 256 uneven squares
 // 9.96-9.98).
 constexpr int kGroup = 16;
 
@@ -56,8 +56,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bstep(const Inst *__restrict__ 
     __shared__ __align__(16) long long skp_raw[(sizeof(KP) + 7) / 8];
     const KP &kp = *reinterpret_cast<const KP *>(skp_raw);
     const int nw = nwork[0];
+    // kGroup items at a time where the list gives every block several groups, fewer on
+    // short lists (each block still gets about four groups)
+    const int grp = max(1, min(kGroup, nw / (4 * (int)gridDim.x)));
     int cached = -1;
-    for (int w = blockIdx.x * kGroup; w < nw; w += (w % kGroup == kGroup - 1) ? (gridDim.x - 1) * kGroup + 1 : 1) {
+    for (int w = blockIdx.x * grp; w < nw; w += (w % grp == grp - 1) ? ((int)gridDim.x - 1) * grp + 1 : 1) {
         const int2 it = work[w];
         if (it.x != cached) {
             __syncthreads();
