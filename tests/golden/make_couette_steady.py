@@ -1,6 +1,6 @@
 """Writes couette_steady_oracle.txt: steady thermal Couette channels computed by the FP64
 oracle alone (Sec. VI A set-up with the walls of reading R5), the reference against which
-the warm-started and rest-started GPU channels are judged.
+the warm-started and rest-started GPU channels are compared.
 
 The channels are held-out draws from the distribution of the surrogate's training sweep
 (Pr in [0.5, 2], gamma in [1.1, 1.67], wall Mach number in [0.01, 0.1], tau in [0.6, 1],
